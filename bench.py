@@ -1,0 +1,342 @@
+#!/usr/bin/env python
+"""Benchmark of the fused coupled-LB step on GB300.
+
+Workload (one step = one time step of the whole lattice through every row of
+the hot path): 3D D3Q27 droplet impact on a liquid film, 256^3 sites, FP32,
+periodic in x and y, solid planes z = 0 and z = 255, droplet R = 32 falling at
+0.05 onto a film of depth 32, density ratio 1000, sigma = 1e-3, seeded 1e-4
+perturbation of phi at the interface.  Inputs are synthetic (workloads/).
+
+Metric: MLUPS (million lattice-site updates per second) of the coupled step,
+the roofline fraction of the step kernel against the measured HBM copy
+bandwidth, an end-to-end MLUPS through the C ABI with host buffers, and the
+FP64 oracle on the host cores as a CPU baseline.
+
+Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
+torch.distributed.run, one independent replica per GPU (the lattices do not
+exchange data: replicas only), timing = max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "coupled-lattice MLUPS & % HBM roofline; served solves/s with p50/p99 latency"
+UNIT = "MLUPS"
+CSRC = os.path.join(ROOT, "paper_2512_01027_gb300", "csrc")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=256, help="grid edge of the workload")
+    ap.add_argument("--storage", default="f32")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(CSRC)):
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = max(smax, float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def workload(n: int):
+    R = n / 8.0
+    return W.droplet_film_3d(n=n, R=R, film=R, uz=-0.05, noise=1e-4)
+
+
+def alg_bytes_per_site(Q: int, D: int, store_bytes: int, field_bytes: int) -> int:
+    """Read + write of both population sets and of the P, u state per site update."""
+    return 2 * (2 * Q * store_bytes) + 2 * (1 + D) * field_bytes
+
+
+def cpu_baseline(reps_target_s: float = 10.0):
+    """The FP64 oracle as it stands, on the host cores, on a bounded sample of
+    the workload: the same droplet-on-film case at 64^3 (R = 8), 24 steps."""
+    import oracle
+
+    c = W.droplet_film_3d(n=64, R=8.0, film=8.0, gap=8.0, uz=-0.05, noise=1e-4)
+    o = oracle.Oracle("D3Q27", c.shape, oracle.make_params(**c.params), periodic=c.periodic, solid=c.solid)
+    o.init(c.phi0, c.P0, c.u0)
+    o.step(1)
+    steps = 24
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return {"value": c.N * steps / dt / 1e6, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"FP64 C oracle, D3Q27 droplet on film 64^3 (R = 8), {steps} steps, {dt:.1f} s"}
+
+
+def dist_init():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def reduce_max(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2512_01027_gb300 as lbm
+
+    world, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    c = workload(args.n)
+    prm = {k: v for k, v in c.params.items() if k != "g_ext"}
+    L = lbm.Lattice(c.lattice, c.shape, periodic=c.periodic, solid=c.solid, storage=args.storage,
+                    g_ext=c.params["g_ext"], **prm)
+    stream = torch.cuda.current_stream()
+    L.set_stream(stream)
+    L.init_fields(c.phi0, c.P0, c.u0)
+    L.step(args.warmup)
+    torch.cuda.synchronize()
+
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    ev0.record(stream)
+    L.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    L.check()
+    ms_max = reduce_max(ms, world)
+    N = c.N
+    value = N * args.steps * world / (ms_max / 1e3) / 1e6
+
+    store_b = {"f64": 8, "f32": 4, "f16": 2, "bf16": 2}[args.storage]
+    field_b = 8 if args.storage == "f64" else 4
+    per_site = alg_bytes_per_site(L.Q, L.d, store_b, field_b)
+    per_launch = per_site * N
+    t_launch = ms / args.steps / 1e3
+    achieved = per_launch / t_launch / 1e9
+    peak, peak_kind = measured_peaks()
+    traffic = None
+    try:
+        with open(TRAFFIC_FILE) as f:
+            tr = json.load(f)
+        if tr.get("source_hash") == kernel_source_hash() and tr.get("n") == args.n and \
+                tr.get("storage") == args.storage:
+            traffic = tr["dram_bytes_per_launch"]
+    except Exception:
+        traffic = None
+
+    e2e = None
+    if not args.no_e2e:
+        # end to end through the C ABI: host fields (pinned) -> device -> K steps -> host fields
+        ke = max(20, args.steps // 4)
+        phi_h = torch.from_numpy(np.ascontiguousarray(c.phi0.reshape(-1))).pin_memory()
+        P_h = torch.from_numpy(np.ascontiguousarray(c.P0.reshape(-1))).pin_memory()
+        u_h = torch.from_numpy(np.ascontiguousarray(c.u0.reshape(3, -1))).pin_memory()
+        out_phi = torch.empty(N, dtype=torch.float64).pin_memory()
+        out_P = torch.empty(N, dtype=torch.float64).pin_memory()
+        out_u = torch.empty(3 * N, dtype=torch.float64).pin_memory()
+        import ctypes
+
+        dptr = ctypes.POINTER(ctypes.c_double)
+        cast = lambda t: ctypes.cast(t.data_ptr(), dptr)  # noqa: E731
+        lib = lbm.lib()
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        rc = lib.lbm_init_fields(L.handle, cast(phi_h), cast(P_h), cast(u_h))
+        rc |= lib.lbm_step(L.handle, ke)
+        rc |= lib.lbm_read_fields(L.handle, cast(out_phi), cast(out_P), cast(out_u))
+        t_e2e = time.perf_counter() - t0
+        barrier(world)
+        if rc != 0:
+            raise RuntimeError(lib.lbm_last_error(L.handle))
+        t_e2e = reduce_max(t_e2e, world)
+        e2e = {"value": N * ke * world / t_e2e / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(5 * 8 * N / ke), "d2h_bytes_per_step": int(5 * 8 * N / ke),
+               "solve": f"init_fields from pinned host fields, {ke} steps, read_fields to pinned host"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"f64": "f64", "f32": "f32", "f16": "f16-storage/f32", "bf16": "bf16-storage/f32"}[args.storage],
+            "data": "synthetic",
+            "config": {"workload": f"D3Q27 droplet impact on a liquid film, {args.n}^3, {args.storage} storage",
+                       "lattice": "D3Q27", "grid": [args.n] * 3, "storage": args.storage,
+                       "parallelism": f"replicas x{world}",
+                       "l2": f"inputs larger than L2 ({(L.footprint()[0]) / 1e9:.1f} GB state per lattice)"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "peak_kind": peak_kind, "kernel": "step_kernel (fused S0..S5, one launch per step)",
+                         "bytes_per_site": per_site},
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def run_reference(args):
+    """The FP64 oracle timed on the host cores as the reference arm: each step
+    is one oracle step on a bounded sample of the workload (the same case at
+    48^3, R = 6)."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    c = W.droplet_film_3d(n=48, R=6.0, film=6.0, gap=8.0, uz=-0.05, noise=1e-4)
+    o = oracle.Oracle("D3Q27", c.shape, oracle.make_params(**c.params), periodic=c.periodic, solid=c.solid)
+    o.init(c.phi0, c.P0, c.u0)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    value = c.N * args.steps / dt / 1e6
+    sample = f"FP64 C oracle, D3Q27 droplet on film 48^3 (R = 6), {args.steps} steps"
+    line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"D3Q27 droplet impact on a liquid film, {args.n}^3, {args.storage} storage",
+                       "lattice": "D3Q27", "grid": [args.n] * 3, "storage": args.storage},
+            "impl": "reference",
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

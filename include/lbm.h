@@ -1,0 +1,195 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) coupled multiphase lattice Boltzmann step.
+ *
+ * Method: Otomo et al., "Lattice Boltzmann models for the hydrodynamic equations
+ * in multiphase flow with high density ratio" (arXiv 2512.01027), Sec. II:
+ *   - phase-field LB for the conservative Allen-Cahn equation, populations h_i
+ *     (Eq. LB_phi_filter_col, h_eq with Gamma_i, theta and the delta-theta
+ *     correction);
+ *   - hydrodynamic LB of the pressure P and velocity u, populations g_i, with the
+ *     LKS-mapped moments (Eq. Kiterm and the P, u definitions), the equilibrium of
+ *     Eq. BGK_LBeq_hydroeq (surface-tension force, density-gradient stress term,
+ *     bulk term B) and the filter collision (Eqs. momentum_flux0/1, LB_filter_col).
+ * One call of lbm_step advances both populations by one time step per site in a
+ * single fused CUDA kernel launch.
+ *
+ * Conventions (all entry points):
+ *   - Every function returns an int status: LBM_OK (0) or one of the LBM_ERR_*
+ *     codes.  On error, lbm_last_error(handle) describes the failure.
+ *   - A handle owns all device memory it allocates; the caller owns every host
+ *     array it passes.  Host arrays are never retained after a call returns.
+ *   - Grid: nx * ny * nz = N sites, x fastest, then y, then z.  2D lattices need
+ *     nz == 1.  Host scalar fields are double[N]; host vector fields are
+ *     double[3][N] (three component planes; the z plane is ignored on input and
+ *     zero on output for 2D lattices).
+ *   - Non-periodic axes are closed by solid sites just outside the grid.  Solid
+ *     sites (grid.solid) are never updated; halfway bounce-back applies on every
+ *     link into a solid site (paper: no-slip walls).
+ *   - Work is enqueued on the handle's stream (default: the legacy default
+ *     stream, or the stream set by lbm_set_stream).  Functions that return host
+ *     data synchronise that stream.
+ *   - There is no CPU fallback: without a usable CUDA device, lbm_create returns
+ *     LBM_ERR_CUDA.
+ *   - Not thread-safe per handle; distinct handles may be used from distinct
+ *     threads.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_ABI_VERSION 1
+
+/* Status codes. */
+#define LBM_OK 0
+#define LBM_ERR_INVALID_ARG 1   /* bad pointer, size, enum or parameter value */
+#define LBM_ERR_OOM 2           /* device allocation failed (cudaMalloc or the allocator hook) */
+#define LBM_ERR_CUDA 3          /* a CUDA runtime call or kernel launch failed */
+#define LBM_ERR_NONFINITE 4     /* a step produced a non-finite phi, P or u */
+#define LBM_ERR_UNSUPPORTED 5   /* valid request this build does not implement */
+
+typedef struct lbm_ctx *lbm_handle;
+
+/* Lattices (Sec. II: the paper uses D3Q19; D2Q9 and D3Q27 use the same
+ * formulas with T = 1/3). */
+typedef enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2 } lbm_lattice;
+
+/* Population storage.  F64: FP64 storage and arithmetic.  F32: FP32 storage
+ * and arithmetic.  F16DEV / BF16DEV: populations stored in 16 bits as scaled
+ * deviations from the lattice weights, collided in FP32; P and u in FP32. */
+typedef enum {
+    LBM_STORE_F64 = 0,
+    LBM_STORE_F32 = 1,
+    LBM_STORE_F16DEV = 2,
+    LBM_STORE_BF16DEV = 3
+} lbm_storage;
+
+typedef struct {
+    int32_t nx, ny, nz;       /* sites per axis (>= 1) */
+    int32_t periodic[3];      /* 1: periodic axis; 0: closed by solid outside the grid */
+    const uint8_t *solid;     /* host, N bytes (1 = solid) or NULL for no solid sites */
+} lbm_grid;
+
+/* Physical parameters (lattice units).  Defaults from Sec. II/III are given
+ * by lbm_default_params.  struct_size must be sizeof(lbm_params). */
+typedef struct {
+    uint64_t struct_size;
+    double rho_w;          /* heavy-phase density (phi = 1), rho_water */
+    double rho_a;          /* light-phase density (phi = 0), rho_air = rho_ref */
+    double nu_w, nu_a;     /* kinematic viscosities; tau_k = nu_k / T + 1/2 (Eq. tau_interpolate) */
+    double sigma;          /* surface tension in the chemical potential mu */
+    double M;              /* mobility; tau_phi = M / T + 1/2 (Eq. LB_phi_filter_col) */
+    double W;              /* interface thickness */
+    double lambda_b;       /* bulk viscosity (paper: 1/6) */
+    double gamma, phi_n, phi_m, D, eps;   /* delta-theta constants (paper: -22.5, 0.8, 0.2, 1e-4, 1e-10) */
+    double g_ext[3];       /* body acceleration; F_ext = rho * g_ext */
+    int32_t clamp_phi_props;   /* 1: clamp phi to [0,1] for rho, tau_mix and omega (default) */
+    int32_t filter_full_trace; /* 0: filter carries the trace-free part of Pi (default);
+                                  1: the full Pi as printed (linearly unstable at low nu) */
+    int32_t storage;           /* lbm_storage of the populations (default LBM_STORE_F32) */
+    int32_t reserved;          /* must be 0 */
+} lbm_params;
+
+/* Fill *p with the paper's defaults: rho_w = 1, rho_a = 1e-3, nu_w = 0.0167,
+ * nu_a = 0.167, sigma = 1e-3, M = 0.166, W = 4, lambda_b = 1/6, gamma = -22.5,
+ * phi_n = 0.8, phi_m = 0.2, D = 1e-4, eps = 1e-10, g_ext = 0, clamp on,
+ * trace-free filter, FP32 storage. */
+int lbm_default_params(lbm_params *p);
+
+/* Direction table of a lattice, in the library's population order (rest
+ * first, then pairs (c, -c)): c[3*i + a] and w[i] for i < Q.  Either output
+ * may be NULL.  *d and *Q receive the dimension and the number of directions. */
+int lbm_lattice_info(int lattice, int *d, int *Q, int *c, double *w);
+
+/* Create a lattice state on the current CUDA device.  grid->solid is copied.
+ * Returns LBM_ERR_INVALID_ARG for bad sizes/parameters (rho_a <= 0,
+ * rho_w <= rho_a, nu <= 0, M <= 0, W <= 0), LBM_ERR_OOM, LBM_ERR_CUDA. */
+int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params, lbm_handle *out);
+
+/* Release all device memory of h (after synchronising its stream). */
+int lbm_destroy(lbm_handle h);
+
+/* Stream for all later work of h (a cudaStream_t passed as void*; NULL = legacy default). */
+int lbm_set_stream(lbm_handle h, void *cuda_stream);
+
+/* Device-memory hooks used by later lbm_create calls in this process: alloc
+ * returns a device pointer of at least `bytes` (256-byte aligned) or NULL;
+ * free releases it.  Pass NULLs to restore cudaMalloc/cudaFree. */
+typedef void *(*lbm_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*lbm_free_fn)(void *ptr, void *ctx);
+int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn free_fn, void *ctx);
+
+/* Initial state from host fields phi[N], P[N], u[3][N]: populations start at
+ * equilibrium (Sec. I: "f_i in the initial condition is assumed to be the
+ * equilibrium state"), h* = h_eq, g* = g_eq built from these fields and their
+ * stencils; P^0 = P, u^0 = u.  Resets the step counter. */
+int lbm_init_fields(lbm_handle h, const double *phi, const double *P, const double *u);
+
+/* Same from device arrays (double, same layout) already on the handle's device. */
+int lbm_init_fields_device(lbm_handle h, const double *d_phi, const double *d_P, const double *d_u);
+
+/* Advance n >= 0 time steps (asynchronous on the handle's stream). */
+int lbm_step(lbm_handle h, int64_t n);
+
+/* Current fields into host arrays (any may be NULL): phi^n = sum_i h*_i,
+ * P^n, u^n (double[3][N]); solid sites read 0.  Synchronises the stream and
+ * returns LBM_ERR_NONFINITE if any step since lbm_init_fields produced a
+ * non-finite value. */
+int lbm_read_fields(lbm_handle h, double *phi, double *P, double *u);
+
+/* Same into device double arrays (no synchronisation). */
+int lbm_read_fields_device(lbm_handle h, double *d_phi, double *d_P, double *d_u);
+
+/* Steps taken since the last lbm_init_fields / lbm_load_state. */
+int lbm_steps_done(lbm_handle h, int64_t *steps);
+
+/* Synchronise and report LBM_ERR_NONFINITE if a non-finite value was seen. */
+int lbm_check(lbm_handle h);
+
+/* FP64 global reductions over fluid sites (Sec. II: sum h_eq = phi makes sum
+ * phi a conserved quantity): out[0] = sum phi, out[1..3] = sum rho(phi) u,
+ * out[4] = number of fluid sites.  Synchronises the stream. */
+int lbm_reduce(lbm_handle h, double out[5]);
+
+/* Laplace pressure jump (Sec. III.A): mean P over fluid sites with
+ * |x - center| < r_in minus mean P over fluid sites with |x - center| > r_out
+ * (distances on the periodic grid; FP64 accumulation).  Synchronises. */
+int lbm_pressure_jump(lbm_handle h, const double center[3], double r_in, double r_out, double *dP);
+
+/* Decoded populations as double[Q][N] in the library's direction order
+ * (lbm_lattice_info), plus P^n and u^n[3][N]; any pointer may be NULL.
+ * Synchronises. */
+int lbm_get_state(lbm_handle h, double *h_pop, double *g_pop, double *P, double *u);
+
+/* State at n chosen sites (linear indices x + nx (y + ny z)): decoded
+ * populations h_pop[n][Q], g_pop[n][Q], P[n] and u[n][3] as doubles, in the
+ * library's direction order; any output may be NULL.  For probes (pressure
+ * sensors) and for sampled checks of large lattices.  Synchronises. */
+int lbm_probe(lbm_handle h, int64_t n, const int64_t *sites, double *h_pop, double *g_pop, double *P, double *u);
+
+/* Checkpoint: raw state bytes (populations in storage format, P, u, step
+ * counter).  lbm_state_bytes gives the size; save/load copy through a host
+ * buffer of exactly that size.  A state loads into a handle of the same
+ * grid, lattice and storage. */
+int lbm_state_bytes(lbm_handle h, size_t *bytes);
+int lbm_save_state(lbm_handle h, void *host_buf, size_t bytes);
+int lbm_load_state(lbm_handle h, const void *host_buf, size_t bytes);
+
+/* Device bytes held by h, and the bytes one step reads and writes at minimum
+ * (algorithmic traffic: both population sets in and out, P and u in and out). */
+int lbm_footprint(lbm_handle h, size_t *device_bytes, size_t *step_bytes);
+
+/* Description of the last error on h (or of the last lbm_create failure when
+ * h is NULL).  Never NULL. */
+const char *lbm_last_error(lbm_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_GB300_H */

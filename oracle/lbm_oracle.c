@@ -229,6 +229,16 @@ static double Gamma(const olat *L, int i, const double u[3])
     return L->w[i] * (1.0 + 3.0 * cu + 4.5 * (cu * cu) - 1.5 * uu);
 }
 
+/* Gamma_i - w_i = w_i { c.u/T + (c.u)^2/(2T^2) - u^2/(2T) }: the same
+ * polynomial without its constant term, the form in which Gamma_i enters
+ * g_eq (evaluated directly, not as a difference of two numbers near w_i). */
+static double Gamma_minus_w(const olat *L, int i, const double u[3])
+{
+    double cu = L->c[i][0] * u[0] + L->c[i][1] * u[1] + L->c[i][2] * u[2];
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    return L->w[i] * (3.0 * cu + 4.5 * (cu * cu) - 1.5 * uu);
+}
+
 /* h_eq_i = phi Gamma_i + theta_tot w_i (c_i . n)  (Sec. II). */
 static void h_equilibrium(const olat *L, double phi, const double u[3], const double n[3],
                           double theta_tot, double *heq)
@@ -261,8 +271,7 @@ static void g_equilibrium(const olat *L, const orc_params *p, double P, double r
         double cF = L->c[i][0] * F[0] + L->c[i][1] * F[1] + L->c[i][2] * F[2];
         double csg = L->c[i][0] * sg[0] + L->c[i][1] * sg[1] + L->c[i][2] * sg[2];
         double v = (i == L->rest) ? P * cP : 0.0;
-        v = v + Gamma(L, i, u);
-        v = v - L->w[i];
+        v = v + Gamma_minus_w(L, i, u);                 /* Gamma_i - w_i */
         v = v + L->w[i] * cF * kF;
         v = v + (L->w[i] - delta) * bdiv;
         v = v + L->w[i] * csg * kS;

@@ -1,0 +1,170 @@
+// Template implementation of the per-(lattice, storage) operations; included
+// by one instantiation unit per precision.
+#pragma once
+
+#include <algorithm>
+
+#include "lbm_internal.h"
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+template <class R>
+inline SiteConsts<R> site_consts(const HostConsts &h)
+{
+    SiteConsts<R> k;
+    k.rho_a = R(h.rho_a); k.drho = R(h.drho); k.om1 = R(h.om1); k.rhoref_T = R(h.rhoref_T);
+    k.cP = R(h.cP); k.tau_a = R(h.tau_a); k.dtau = R(h.dtau); k.inv_tau_phi = R(h.inv_tau_phi);
+    k.lambda_b = R(h.lambda_b); k.M3 = R(h.M3); k.W = R(h.W); k.eps = R(h.eps);
+    k.phi_n = R(h.phi_n); k.phi_m = R(h.phi_m); k.D = R(h.D); k.dt_pref = R(h.dt_pref);
+    k.A_mu = R(h.A_mu); k.B_mu = R(h.B_mu);
+    k.g[0] = R(h.g[0]); k.g[1] = R(h.g[1]); k.g[2] = R(h.g[2]);
+    k.clamp = h.clamp; k.full_trace = h.full_trace;
+    return k;
+}
+
+template <class L, class R, class C>
+struct Impl {
+    using S = typename C::S;
+
+    static size_t step_smem() { return step_smem_bytes<L, R>(); }
+
+    template <bool M>
+    static int launch_step(lbm_ctx *c, const StepArgs<R, S> &a)
+    {
+        using Tl = Tile<L>;
+        const size_t smem = step_smem_bytes<L, R>();
+        static bool attr_set = false;
+        if (!attr_set) {
+            cudaError_t e = cudaFuncSetAttribute(step_kernel<L, R, C, M>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return cuda_fail(c, e, "cudaFuncSetAttribute(step)");
+            attr_set = true;
+        }
+        dim3 block(Tl::SX, Tl::SY, 1);
+        dim3 grid((c->nx + Tl::TX - 1) / Tl::TX, (c->ny + Tl::TY - 1) / Tl::TY,
+                  (L::D == 3) ? (c->nz + c->zchunk - 1) / c->zchunk : 1);
+        step_kernel<L, R, C, M><<<grid, block, smem, c->stream>>>(a);
+        return cuda_fail(c, cudaGetLastError(), "step_kernel launch");
+    }
+
+    static int step(lbm_ctx *c, int64_t n)
+    {
+        StepArgs<R, S> a;
+        a.mask = c->mask;
+        a.err = c->d_err;
+        a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
+        a.per_x = c->periodic[0]; a.per_y = c->periodic[1]; a.per_z = c->periodic[2];
+        a.zchunk = c->zchunk;
+        a.N = c->N;
+        a.k = site_consts<R>(c->consts);
+        for (int64_t s = 0; s < n; ++s) {
+            const int src = c->cur, dst = 1 - c->cur;
+            a.src_h = static_cast<const S *>(c->h[src]);
+            a.src_g = static_cast<const S *>(c->g[src]);
+            a.dst_h = static_cast<S *>(c->h[dst]);
+            a.dst_g = static_cast<S *>(c->g[dst]);
+            a.P_old = static_cast<const R *>(c->P[src]);
+            a.P_new = static_cast<R *>(c->P[dst]);
+            a.u_old = static_cast<const R *>(c->u[src]);
+            a.u_new = static_cast<R *>(c->u[dst]);
+            const int rc = c->has_mask ? launch_step<true>(c, a) : launch_step<false>(c, a);
+            if (rc != LBM_OK) return rc;
+            c->cur = dst;
+            c->steps += 1;
+        }
+        return LBM_OK;
+    }
+
+    static int init(lbm_ctx *c, const double *d_phi, const double *d_P, const double *d_u)
+    {
+        InitArgs<R, S> a;
+        a.phi0 = d_phi; a.P0 = d_P; a.u0 = d_u;
+        a.h = static_cast<S *>(c->h[0]);
+        a.g = static_cast<S *>(c->g[0]);
+        a.P = static_cast<R *>(c->P[0]);
+        a.u = static_cast<R *>(c->u[0]);
+        a.mask = c->mask;
+        a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
+        a.N = c->N;
+        a.k = site_consts<R>(c->consts);
+        const int threads = 128;
+        const unsigned blocks = (unsigned)((c->N + threads - 1) / threads);
+        if (c->has_mask) init_kernel<L, R, C, true><<<blocks, threads, 0, c->stream>>>(a);
+        else init_kernel<L, R, C, false><<<blocks, threads, 0, c->stream>>>(a);
+        c->cur = 0;
+        c->steps = 0;
+        return cuda_fail(c, cudaGetLastError(), "init_kernel launch");
+    }
+
+    static ReadArgs<R, S> read_args(lbm_ctx *c)
+    {
+        ReadArgs<R, S> a;
+        a.h = static_cast<const S *>(c->h[c->cur]);
+        a.g = static_cast<const S *>(c->g[c->cur]);
+        a.P = static_cast<const R *>(c->P[c->cur]);
+        a.u = static_cast<const R *>(c->u[c->cur]);
+        a.mask = c->mask;
+        a.phi_out = a.P_out = a.u_out = a.hpop_out = a.gpop_out = nullptr;
+        a.N = c->N;
+        a.cP = R(c->consts.cP);
+        return a;
+    }
+
+    static int read(lbm_ctx *c, double *d_phi, double *d_P, double *d_u, double *d_hpop, double *d_gpop)
+    {
+        ReadArgs<R, S> a = read_args(c);
+        a.phi_out = d_phi; a.P_out = d_P; a.u_out = d_u; a.hpop_out = d_hpop; a.gpop_out = d_gpop;
+        const int threads = 256;
+        const unsigned blocks = (unsigned)((c->N + threads - 1) / threads);
+        if (c->has_mask) read_kernel<L, R, C, true><<<blocks, threads, 0, c->stream>>>(a);
+        else read_kernel<L, R, C, false><<<blocks, threads, 0, c->stream>>>(a);
+        return cuda_fail(c, cudaGetLastError(), "read_kernel launch");
+    }
+
+    static int reduce(lbm_ctx *c, double *d_out5)
+    {
+        ReadArgs<R, S> a = read_args(c);
+        const int blocks = (int)std::min<long long>(kRedMaxBlocks, (c->N + kRedThreads - 1) / kRedThreads);
+        double *partials = c->d_scratch;
+        if (c->has_mask)
+            reduce_kernel<L, R, C, true><<<blocks, kRedThreads, 0, c->stream>>>(
+                a, R(c->consts.rho_a), R(c->consts.drho), c->consts.clamp, partials);
+        else
+            reduce_kernel<L, R, C, false><<<blocks, kRedThreads, 0, c->stream>>>(
+                a, R(c->consts.rho_a), R(c->consts.drho), c->consts.clamp, partials);
+        finish_kernel<kRedVals><<<1, kRedThreads, 0, c->stream>>>(partials, blocks, d_out5);
+        return cuda_fail(c, cudaGetLastError(), "reduce launch");
+    }
+
+    static int pjump(lbm_ctx *c, const double center[3], double r_in, double r_out, double *d_out4)
+    {
+        const int blocks = (int)std::min<long long>(kRedMaxBlocks, (c->N + kRedThreads - 1) / kRedThreads);
+        double *partials = c->d_scratch;
+        const R *P = static_cast<const R *>(c->P[c->cur]);
+        if (c->has_mask)
+            pjump_kernel<R, true><<<blocks, kRedThreads, 0, c->stream>>>(
+                P, c->mask, c->nx, c->ny, c->nz, c->N, center[0], center[1], center[2], r_in, r_out, partials);
+        else
+            pjump_kernel<R, false><<<blocks, kRedThreads, 0, c->stream>>>(
+                P, c->mask, c->nx, c->ny, c->nz, c->N, center[0], center[1], center[2], r_in, r_out, partials);
+        finish_kernel<4><<<1, kRedThreads, 0, c->stream>>>(partials, blocks, d_out4);
+        return cuda_fail(c, cudaGetLastError(), "pjump launch");
+    }
+
+    static int probe(lbm_ctx *c, const long long *d_sites, int n, double *d_h, double *d_g, double *d_P, double *d_u)
+    {
+        ReadArgs<R, S> a = read_args(c);
+        const int threads = 128;
+        probe_kernel<L, R, C><<<(n + threads - 1) / threads, threads, 0, c->stream>>>(a, d_sites, n, d_h, d_g, d_P, d_u);
+        return cuda_fail(c, cudaGetLastError(), "probe_kernel launch");
+    }
+
+    static const Ops *ops()
+    {
+        static const Ops o = {&init, &step, &read, &reduce, &pjump, &probe, &step_smem};
+        return &o;
+    }
+};
+
+}  // namespace lbm

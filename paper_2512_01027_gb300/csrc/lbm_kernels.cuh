@@ -1,0 +1,526 @@
+// Kernels of the coupled LB step: fused step, initialisation, readout,
+// FP64 reductions.  Templated on lattice L, compute type R and population
+// storage codec C (identity for FP64/FP32, scaled 16-bit deviations for the
+// reduced-storage forms).
+//
+// Fused step (one launch per time step, ping-pong buffers src -> dst):
+//   A CTA owns an interior tile of TX x TY sites in (x, y) and marches in z
+//   over a chunk [zb, ze).  Its threads cover the tile plus a one-site halo
+//   (SX = TX + 2, SY = TY + 2).  For each plane the threads pull the
+//   populations of their site and compute the moments (phi, u^{n+1}, and for
+//   interior sites P^{n+1}) into a three-plane ring in shared memory; the
+//   interior sites also park their pulled populations in shared memory.  One
+//   plane later, when the ring holds phi and u on planes z-1, z, z+1, the
+//   interior threads evaluate the stencils from the ring, collide both
+//   populations and store them.  The halo moments are recomputed by the
+//   neighbouring CTA's threads instead of exchanged, so one launch is one
+//   time step: every population is read from HBM once and written once
+//   (halo re-reads hit L2).
+#pragma once
+
+#include <cstdint>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include "lbm_lattice.cuh"
+#include "lbm_site.cuh"
+
+namespace lbm {
+
+constexpr uint32_t kSolidBit = 1u << 31;
+
+// ---------------------------------------------------------------------------
+// Storage codecs
+
+// Identity storage (FP64 / FP32): populations stored as computed.
+template <class R>
+struct CodecId {
+    using S = R;
+    template <int i>
+    __device__ __forceinline__ static R dec_h(S v) { return v; }
+    template <int i>
+    __device__ __forceinline__ static S enc_h(R v) { return v; }
+    template <int i>
+    __device__ __forceinline__ static R dec_g(S v, R /*P_site*/, R /*cP*/) { return v; }
+    template <int i>
+    __device__ __forceinline__ static S enc_g(R v, R /*P_site*/, R /*cP*/) { return v; }
+};
+
+// ---------------------------------------------------------------------------
+// Kernel arguments
+
+template <class R, class S>
+struct StepArgs {
+    const S *src_h;
+    const S *src_g;
+    S *dst_h;
+    S *dst_g;
+    const R *P_old;
+    R *P_new;
+    const R *u_old;      // [D][N]
+    R *u_new;            // [D][N]
+    const uint32_t *mask;  // [N] or nullptr
+    int *err;
+    int nx, ny, nz;
+    int per_x, per_y, per_z;
+    int zchunk;
+    long long N;
+    SiteConsts<R> k;
+};
+
+__device__ __forceinline__ int wrapc(int v, int n)
+{
+    return v < 0 ? v + n : (v >= n ? v - n : v);
+}
+
+template <class L>
+struct Tile {
+    static constexpr int SX = 32;
+    static constexpr int SY = 8;
+    static constexpr int TX = SX - 2;
+    static constexpr int TY = SY - 2;
+    static constexpr int TI = TX * TY;
+    static constexpr int RING = (L::D == 3) ? 3 : 1;
+    static constexpr int STASH = (L::D == 3) ? 2 : 1;
+    static constexpr int NT = SX * SY;
+};
+
+template <class L, class R>
+__host__ __device__ constexpr size_t step_smem_bytes()
+{
+    using Tl = Tile<L>;
+    return sizeof(R) * (size_t)(Tl::RING * Tl::SX * Tl::SY * (1 + L::D)         // ring phi, u
+                                + Tl::STASH * Tl::TI * (2 * L::Q + 3))          // stash hp, gp, P, rho, phihat
+           + sizeof(uint32_t) * (size_t)(Tl::STASH * Tl::TI);                  // stash mask
+}
+
+// ---------------------------------------------------------------------------
+// Fused step kernel
+
+template <class L, class R, class C, bool HAS_MASK>
+__global__ void __launch_bounds__(Tile<L>::NT)
+step_kernel(const StepArgs<R, typename C::S> a)
+{
+    using S = typename C::S;
+    using Tl = Tile<L>;
+    constexpr int D = L::D, Q = L::Q;
+    constexpr int SX = Tl::SX, SY = Tl::SY, TX = Tl::TX, TY = Tl::TY, TI = Tl::TI;
+    constexpr int PL = SX * SY;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *ring_phi = reinterpret_cast<R *>(smem_raw);
+    R *ring_u = ring_phi + Tl::RING * PL;
+    R *st_h = ring_u + Tl::RING * D * PL;
+    R *st_g = st_h + Tl::STASH * Q * TI;
+    R *st_P = st_g + Tl::STASH * Q * TI;
+    R *st_rho = st_P + Tl::STASH * TI;
+    R *st_ph = st_rho + Tl::STASH * TI;
+    uint32_t *st_m = reinterpret_cast<uint32_t *>(st_ph + Tl::STASH * TI);
+
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int X0 = blockIdx.x * TX, Y0 = blockIdx.y * TY;
+    const int xs = X0 - 1 + tx, ys = Y0 - 1 + ty;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const long long N = a.N;
+    const int zb = (D == 3) ? blockIdx.z * a.zchunk : 0;
+    const int ze = (D == 3) ? min(nz, zb + a.zchunk) : 1;
+    const bool in_tile = (tx >= 1 && tx <= TX && ty >= 1 && ty <= TY && xs < nx && ys < ny);
+    const int ti = (ty - 1) * TX + (tx - 1);
+
+    // (x, y) of this thread's S1 site, wrapped; validity in x, y
+    bool xy_ok = true;
+    int xw = xs, yw = ys;
+    if (xs < 0 || xs >= nx) { if (a.per_x) xw = wrapc(xs, nx); else xy_ok = false; }
+    if (ys < 0 || ys >= ny) { if (a.per_y) yw = wrapc(ys, ny); else xy_ok = false; }
+    // source offsets x - c, c in {-1, 0, 1}: xo[1 - c]
+    int xo[3], yo[3];
+    xo[0] = wrapc(xw - 1, nx); xo[1] = xw; xo[2] = wrapc(xw + 1, nx);
+    yo[0] = wrapc(yw - 1, ny) * nx; yo[1] = yw * nx; yo[2] = wrapc(yw + 1, ny) * nx;
+
+    const int z_first = (D == 3) ? zb - 1 : 0;
+    const int z_last = (D == 3) ? ze : 0;
+    for (int zz = z_first; zz <= z_last; ++zz) {
+        // ---------------- S0 + S1 on plane zz ----------------
+        {
+            bool ok = xy_ok;
+            int zw = zz;
+            if (D == 3 && (zz < 0 || zz >= nz)) { if (a.per_z) zw = wrapc(zz, nz); else ok = false; }
+            const bool interior = in_tile && zz >= zb && zz < ze;
+            if (ok) {
+                const long long plane = (long long)zw * nx * ny;
+                const long long idx = plane + yo[1] + xo[1];
+                uint32_t m = 0;
+                if constexpr (HAS_MASK) m = a.mask[idx];
+                if (!(m & kSolidBit)) {
+                    long long zo[3];
+                    if constexpr (D == 3) {
+                        zo[0] = (long long)wrapc(zw - 1, nz) * nx * ny;
+                        zo[1] = plane;
+                        zo[2] = (long long)wrapc(zw + 1, nz) * nx * ny;
+                    } else {
+                        zo[0] = zo[1] = zo[2] = 0;
+                    }
+                    R hp[Q], gp[Q], Pn[Q], K[Q];
+                    const R P0 = a.P_old[idx];
+                    R sum_wcu = R(0);
+                    static_for<0, Q>([&](auto I) {
+                        constexpr int i = decltype(I)::value;
+                        constexpr int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+                        if constexpr (i == 0) {
+                            hp[0] = C::template dec_h<0>(a.src_h[idx]);
+                            gp[0] = C::template dec_g<0>(a.src_g[idx], P0, a.k.cP);
+                            Pn[0] = P0;
+                        } else {
+                            const long long src = zo[1 - cz] + yo[1 - cy] + xo[1 - cx];
+                            const bool solid_src = HAS_MASK && ((m >> i) & 1u);
+                            if (solid_src) {
+                                // halfway bounce-back: h_i(x) = h*_{-i}(x)
+                                hp[i] = C::template dec_h<opp(i)>(a.src_h[(long long)opp(i) * N + idx]);
+                                gp[i] = C::template dec_g<opp(i)>(a.src_g[(long long)opp(i) * N + idx], P0, a.k.cP);
+                                Pn[i] = P0;
+                            } else {
+                                hp[i] = C::template dec_h<i>(a.src_h[(long long)i * N + src]);
+                                gp[i] = C::template dec_g<i>(a.src_g[(long long)i * N + src], R(0), a.k.cP);
+                                Pn[i] = a.P_old[src];
+                                if (interior) {
+                                    R un[3];
+                                    static_for<0, D>([&](auto A) {
+                                        constexpr int ax = decltype(A)::value;
+                                        if constexpr (L::c(i, ax) != 0) un[ax] = a.u_old[(long long)ax * N + src];
+                                        else un[ax] = R(0);
+                                    });
+                                    if constexpr (D == 2) un[2] = R(0);
+                                    sum_wcu = sum_wcu + R(L::w(i)) * dot_c<L, i>(un);
+                                }
+                            }
+                        }
+                    });
+                    R phi, phihat, rho, u[3];
+                    s1_moments<L, R>(a.k, hp, gp, Pn, P0, phi, phihat, rho, u, K);
+                    const int rs = (D == 3) ? (zz + 3) % 3 : 0;
+                    ring_phi[rs * PL + ty * SX + tx] = phi;
+                    static_for<0, D>([&](auto A) {
+                        constexpr int ax = decltype(A)::value;
+                        ring_u[(rs * D + ax) * PL + ty * SX + tx] = u[ax];
+                    });
+                    if (interior) {
+                        const R Pnew = s1_pressure<L, R>(a.k, gp, K, rho, sum_wcu);
+                        const int ss = (D == 3) ? (zz & 1) : 0;
+                        static_for<0, Q>([&](auto I) {
+                            constexpr int i = decltype(I)::value;
+                            st_h[(ss * Q + i) * TI + ti] = hp[i];
+                            st_g[(ss * Q + i) * TI + ti] = gp[i];
+                        });
+                        st_P[ss * TI + ti] = Pnew;
+                        st_rho[ss * TI + ti] = rho;
+                        st_ph[ss * TI + ti] = phihat;
+                        st_m[ss * TI + ti] = m;
+                    }
+                } else if (interior) {
+                    const int ss = (D == 3) ? (zz & 1) : 0;
+                    st_m[ss * TI + ti] = m;
+                }
+            } else if (interior) {
+                const int ss = (D == 3) ? (zz & 1) : 0;
+                st_m[ss * TI + ti] = kSolidBit;
+            }
+        }
+        __syncthreads();
+        // ---------------- S2..S5 on plane zc ----------------
+        const int zc = (D == 3) ? zz - 1 : zz;
+        if (zc >= zb && in_tile) {
+            const int ss = (D == 3) ? (zc & 1) : 0;
+            const uint32_t m = st_m[ss * TI + ti];
+            if (!(m & kSolidBit)) {
+                const int r0 = (D == 3) ? (zc + 3) % 3 : 0;
+                const int rm = (D == 3) ? (zc + 2) % 3 : 0;
+                const int rp = (D == 3) ? (zc + 4) % 3 : 0;
+                const int c0 = ty * SX + tx;
+                auto ring_at = [&](const R *base, int plane_stride, auto I, int s) -> R {
+                    constexpr int i = decltype(I)::value;
+                    constexpr int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+                    const int r = (cz == 0) ? r0 : ((cz * s > 0) ? rp : rm);
+                    return base[r * plane_stride + c0 + s * (cy * SX + cx)];
+                };
+                const R phi = ring_phi[r0 * PL + c0];
+                R gphi[3], lphi;
+                stencil<L, R>([&](auto I, int s) { return ring_at(ring_phi, PL, I, s); }, m, phi, phi, gphi, lphi);
+                R u[3], gu[3][3];
+                u[2] = R(0);
+                gu[0][2] = gu[1][2] = gu[2][0] = gu[2][1] = gu[2][2] = R(0);
+                static_for<0, D>([&](auto A) {
+                    constexpr int ax = decltype(A)::value;
+                    const R *base = ring_u + ax * PL;
+                    u[ax] = base[r0 * D * PL + c0];
+                    R lap_unused;
+                    stencil<L, R>([&](auto I, int s) { return ring_at(base, D * PL, I, s); }, m, u[ax], R(0),
+                                  gu[ax], lap_unused);
+                });
+                const R P = st_P[ss * TI + ti];
+                const R rho = st_rho[ss * TI + ti];
+                const R phihat = st_ph[ss * TI + ti];
+                R hp[Q], gp[Q], hs[Q], gs[Q];
+                static_for<0, Q>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    hp[i] = st_h[(ss * Q + i) * TI + ti];
+                    gp[i] = st_g[(ss * Q + i) * TI + ti];
+                });
+                collide<L, R, false>(a.k, phi, phihat, rho, P, u, gphi, lphi, gu, hp, gp, hs, gs);
+                const long long idx = (long long)zc * nx * ny + (long long)ys * nx + xs;
+                static_for<0, Q>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    a.dst_h[(long long)i * N + idx] = C::template enc_h<i>(hs[i]);
+                    a.dst_g[(long long)i * N + idx] = C::template enc_g<i>(gs[i], P, a.k.cP);
+                });
+                a.P_new[idx] = P;
+                static_for<0, D>([&](auto A) {
+                    constexpr int ax = decltype(A)::value;
+                    a.u_new[(long long)ax * N + idx] = u[ax];
+                });
+                if (!(isfinite(phi) && isfinite(P) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2])))
+                    atomicOr(a.err, 1);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Initialisation: populations at equilibrium from (phi0, P0, u0) (double).
+
+template <class R, class S>
+struct InitArgs {
+    const double *phi0, *P0, *u0;  // u0: [3][N]
+    S *h, *g;
+    R *P, *u;                      // u: [D][N]
+    const uint32_t *mask;
+    int nx, ny, nz;
+    long long N;
+    SiteConsts<R> k;
+};
+
+template <class L, class R, class C, bool HAS_MASK>
+__global__ void __launch_bounds__(128) init_kernel(const InitArgs<R, typename C::S> a)
+{
+    constexpr int D = L::D, Q = L::Q;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= a.N) return;
+    uint32_t m = 0;
+    if constexpr (HAS_MASK) m = a.mask[idx];
+    if (m & kSolidBit) return;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int x = (int)(idx % nx);
+    const int y = (int)((idx / nx) % ny);
+    const int z = (int)(idx / ((long long)nx * ny));
+    // neighbour x + s c_i (wrapped; a solid/outside neighbour is flagged by the mask)
+    auto nb = [&](auto I, int s) -> long long {
+        constexpr int i = decltype(I)::value;
+        const int xx = wrapc(x + s * L::c(i, 0), nx);
+        const int yy = wrapc(y + s * L::c(i, 1), ny);
+        const int zz = (D == 3) ? wrapc(z + s * L::c(i, 2), nz) : 0;
+        return ((long long)zz * ny + yy) * nx + xx;
+    };
+    const R phi = R(a.phi0[idx]);
+    const R phihat = a.k.clamp ? clamp01(phi) : phi;
+    const R rho = a.k.rho_a + phihat * a.k.drho;
+    R gphi[3], lphi;
+    stencil<L, R>([&](auto I, int s) { return R(a.phi0[nb(I, s)]); }, m, phi, phi, gphi, lphi);
+    R u[3], gu[3][3];
+    u[2] = R(0);
+    gu[0][2] = gu[1][2] = gu[2][0] = gu[2][1] = gu[2][2] = R(0);
+    static_for<0, D>([&](auto A) {
+        constexpr int ax = decltype(A)::value;
+        const double *f = a.u0 + (long long)ax * a.N;
+        u[ax] = R(f[idx]);
+        R lap_unused;
+        stencil<L, R>([&](auto I, int s) { return R(f[nb(I, s)]); }, m, u[ax], R(0), gu[ax], lap_unused);
+    });
+    const R P = R(a.P0[idx]);
+    R hs[Q], gs[Q];
+    collide<L, R, true>(a.k, phi, phihat, rho, P, u, gphi, lphi, gu, nullptr, nullptr, hs, gs);
+    static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        a.h[(long long)i * a.N + idx] = C::template enc_h<i>(hs[i]);
+        a.g[(long long)i * a.N + idx] = C::template enc_g<i>(gs[i], P, a.k.cP);
+    });
+    a.P[idx] = P;
+    static_for<0, D>([&](auto A) {
+        constexpr int ax = decltype(A)::value;
+        a.u[(long long)ax * a.N + idx] = u[ax];
+    });
+}
+
+// ---------------------------------------------------------------------------
+// Readout: phi = sum_i h*_i, P, u as double (solid sites 0).
+
+template <class R, class S>
+struct ReadArgs {
+    const S *h, *g;
+    const R *P, *u;
+    const uint32_t *mask;
+    double *phi_out, *P_out, *u_out;   // u_out: [3][N]
+    double *hpop_out, *gpop_out;       // optional decoded populations [Q][N]
+    long long N;
+    R cP;
+};
+
+template <class L, class R, class C, bool HAS_MASK>
+__global__ void __launch_bounds__(256) read_kernel(const ReadArgs<R, typename C::S> a)
+{
+    constexpr int D = L::D, Q = L::Q;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= a.N) return;
+    bool solid = false;
+    if constexpr (HAS_MASK) solid = (a.mask[idx] & kSolidBit) != 0;
+    const R P = solid ? R(0) : a.P[idx];
+    if (a.phi_out) {
+        R phi = R(0);
+        if (!solid) {
+            phi = C::template dec_h<0>(a.h[idx]);
+            static_for<1, Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                phi = phi + C::template dec_h<i>(a.h[(long long)i * a.N + idx]);
+            });
+        }
+        a.phi_out[idx] = (double)phi;
+    }
+    if (a.P_out) a.P_out[idx] = (double)P;
+    if (a.u_out) {
+        static_for<0, 3>([&](auto A) {
+            constexpr int ax = decltype(A)::value;
+            double v = 0.0;
+            if (ax < D && !solid) v = (double)a.u[(long long)(ax < D ? ax : 0) * a.N + idx];
+            a.u_out[(long long)ax * a.N + idx] = v;
+        });
+    }
+    if (a.hpop_out || a.gpop_out) {
+        static_for<0, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            if (a.hpop_out) a.hpop_out[(long long)i * a.N + idx] =
+                solid ? 0.0 : (double)C::template dec_h<i>(a.h[(long long)i * a.N + idx]);
+            if (a.gpop_out) a.gpop_out[(long long)i * a.N + idx] =
+                solid ? 0.0 : (double)C::template dec_g<i>(a.g[(long long)i * a.N + idx], P, a.cP);
+        });
+    }
+}
+
+// Gather of the state at chosen sites (decoded, double).
+template <class L, class R, class C>
+__global__ void __launch_bounds__(128) probe_kernel(const ReadArgs<R, typename C::S> a, const long long *sites, int n,
+                                                    double *hp, double *gp, double *P, double *u)
+{
+    constexpr int D = L::D, Q = L::Q;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const long long idx = sites[j];
+    if (idx < 0 || idx >= a.N) return;
+    const R Ps = a.P[idx];
+    if (P) P[j] = (double)Ps;
+    if (u) {
+        static_for<0, 3>([&](auto A) {
+            constexpr int ax = decltype(A)::value;
+            u[(long long)j * 3 + ax] = (ax < D) ? (double)a.u[(long long)(ax < D ? ax : 0) * a.N + idx] : 0.0;
+        });
+    }
+    static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        if (hp) hp[(long long)j * Q + i] = (double)C::template dec_h<i>(a.h[(long long)i * a.N + idx]);
+        if (gp) gp[(long long)j * Q + i] = (double)C::template dec_g<i>(a.g[(long long)i * a.N + idx], Ps, a.cP);
+    });
+}
+
+// ---------------------------------------------------------------------------
+// FP64 reductions, deterministic two-pass: per-block partials, then one block
+// sums the partials in a fixed order.
+
+constexpr int kRedThreads = 256;
+constexpr int kRedMaxBlocks = 1024;
+constexpr int kRedVals = 5;
+
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double *sh /* [NV][kRedThreads] */)
+{
+    const int t = threadIdx.x;
+    for (int j = 0; j < NV; ++j) sh[j * kRedThreads + t] = v[j];
+    __syncthreads();
+    for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+        if (t < s)
+            for (int j = 0; j < NV; ++j) sh[j * kRedThreads + t] += sh[j * kRedThreads + t + s];
+        __syncthreads();
+    }
+    for (int j = 0; j < NV; ++j) v[j] = sh[j * kRedThreads];
+}
+
+// sums: phi, rho u_x, rho u_y, rho u_z, fluid sites
+template <class L, class R, class C, bool HAS_MASK>
+__global__ void __launch_bounds__(kRedThreads) reduce_kernel(const ReadArgs<R, typename C::S> a, R rho_a, R drho,
+                                                             int clamp, double *partials)
+{
+    constexpr int D = L::D, Q = L::Q;
+    __shared__ double sh[kRedVals * kRedThreads];
+    double v[kRedVals] = {0, 0, 0, 0, 0};
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < a.N;
+         idx += (long long)gridDim.x * blockDim.x) {
+        if constexpr (HAS_MASK)
+            if (a.mask[idx] & kSolidBit) continue;
+        double phi = 0.0;
+        static_for<0, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            phi += (double)C::template dec_h<i>(a.h[(long long)i * a.N + idx]);
+        });
+        const double ph = clamp ? fmin(1.0, fmax(0.0, phi)) : phi;
+        const double rho = (double)rho_a + ph * (double)drho;
+        v[0] += phi;
+        static_for<0, D>([&](auto A) {
+            constexpr int ax = decltype(A)::value;
+            v[1 + ax] += rho * (double)a.u[(long long)ax * a.N + idx];
+        });
+        v[4] += 1.0;
+    }
+    block_sum<kRedVals>(v, sh);
+    if (threadIdx.x == 0)
+        for (int j = 0; j < kRedVals; ++j) partials[(long long)blockIdx.x * kRedVals + j] = v[j];
+}
+
+// Laplace jump sums: P inside r_in, count inside, P outside r_out, count outside.
+template <class R, bool HAS_MASK>
+__global__ void __launch_bounds__(kRedThreads) pjump_kernel(const R *P, const uint32_t *mask, int nx, int ny, int nz,
+                                                            long long N, double cx, double cy, double cz, double r_in,
+                                                            double r_out, double *partials)
+{
+    __shared__ double sh[4 * kRedThreads];
+    double v[4] = {0, 0, 0, 0};
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < N;
+         idx += (long long)gridDim.x * blockDim.x) {
+        if constexpr (HAS_MASK)
+            if (mask[idx] & kSolidBit) continue;
+        const int x = (int)(idx % nx), y = (int)((idx / nx) % ny), z = (int)(idx / ((long long)nx * ny));
+        double dx = fabs(x - cx), dy = fabs(y - cy), dz = fabs(z - cz);
+        dx = fmin(dx, nx - dx);
+        dy = fmin(dy, ny - dy);
+        dz = fmin(dz, nz - dz);
+        const double r = sqrt(dx * dx + dy * dy + dz * dz);
+        const double p = (double)P[idx];
+        if (r < r_in) { v[0] += p; v[1] += 1.0; }
+        if (r > r_out) { v[2] += p; v[3] += 1.0; }
+    }
+    block_sum<4>(v, sh);
+    if (threadIdx.x == 0)
+        for (int j = 0; j < 4; ++j) partials[(long long)blockIdx.x * 4 + j] = v[j];
+}
+
+// Second pass: one block adds nblocks partial vectors of NV values in a fixed order.
+template <int NV>
+__global__ void __launch_bounds__(kRedThreads) finish_kernel(const double *partials, int nblocks, double *out)
+{
+    __shared__ double sh[NV * kRedThreads];
+    double v[NV];
+    for (int j = 0; j < NV; ++j) v[j] = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+        for (int j = 0; j < NV; ++j) v[j] += partials[(long long)b * NV + j];
+    block_sum<NV>(v, sh);
+    if (threadIdx.x == 0)
+        for (int j = 0; j < NV; ++j) out[j] = v[j];
+}
+
+}  // namespace lbm

@@ -1,0 +1,318 @@
+// Per-site arithmetic of the coupled LB step (Otomo et al., Sec. II).
+//
+// Every formula is evaluated in one fixed order: the order the paper writes
+// its terms, with T = 1/3 substituted exactly (1/T = 3, 1/(2T) = 3/2,
+// 1/(2T^2) = 9/2, 2/T = 6, T/2 = 1/6), sums over directions in ascending
+// direction index, and terms whose lattice coefficient c is 0 dropped (they
+// only add +-0).  Built without FMA contraction (FP64 units) this reproduces,
+// operation for operation, any FP64 evaluation that follows the same order;
+// the method is not Lipschitz where |grad phi| -> 0 (the unit normal n) or
+// lap phi -> 0 (the sign s of delta-theta), so FP64 results of two
+// implementations only stay equal when their rounding is identical.
+#pragma once
+
+#include "lbm_lattice.cuh"
+
+namespace lbm {
+
+// Run constants, precomputed on the host in double and converted to R.
+template <class R>
+struct SiteConsts {
+    R rho_a;        // rho_air = rho_ref
+    R drho;         // rho_w - rho_a
+    R om1;          // omega_max - 1 = rho_w / rho_a - 1
+    R rhoref_T;     // rho_ref * T
+    R cP;           // 1 / (rho_ref T) = 3 / rho_a
+    R tau_a;        // nu_a / T + 1/2
+    R dtau;         // tau_w - tau_a
+    R inv_tau_phi;  // 1 / (M / T + 1/2)
+    R lambda_b;
+    R M3;           // M / T
+    R W;
+    R eps;
+    R phi_n, phi_m, D;
+    R dt_pref;      // gamma M / (T W)
+    R A_mu;         // 48 sigma / W
+    R B_mu;         // 3 sigma W / 2
+    R g[3];         // body acceleration
+    int clamp;
+    int full_trace;
+};
+
+template <class R>
+__device__ __forceinline__ R clamp01(R v)
+{
+    return fmin(R(1), fmax(R(0), v));
+}
+
+// First direction component with c != 0 (3 if none).
+template <class L, int i>
+__host__ __device__ constexpr int first_nz()
+{
+    return L::c(i, 0) ? 0 : (L::c(i, 1) ? 1 : (L::c(i, 2) ? 2 : 3));
+}
+
+// c_i . v = (c_0 v_0 + c_1 v_1) + c_2 v_2 with the zero terms dropped.
+template <class L, int i, class R>
+__device__ __forceinline__ R dot_c(const R *v)
+{
+    constexpr int f = first_nz<L, i>();
+    if constexpr (f == 3) {
+        return R(0);
+    } else {
+        R acc = (L::c(i, f) > 0) ? v[f] : -v[f];
+        static_for<f + 1, 3>([&](auto A) {
+            constexpr int a = decltype(A)::value;
+            if constexpr (L::c(i, a) > 0) acc = acc + v[a];
+            else if constexpr (L::c(i, a) < 0) acc = acc - v[a];
+        });
+        return acc;
+    }
+}
+
+// acc += t * c_ia  (c in {-1, 0, 1})
+template <int ca, class R>
+__device__ __forceinline__ void acc_c(R &acc, R t)
+{
+    if constexpr (ca > 0) acc = acc + t;
+    else if constexpr (ca < 0) acc = acc - t;
+}
+
+// Gamma_i = w_i { 1 + c.u/T + (c.u)^2/(2T^2) - u^2/(2T) }   (Sec. II)
+template <class L, int i, class R>
+__device__ __forceinline__ R gamma_i(const R *u, R uu)
+{
+    const R cu = dot_c<L, i>(u);
+    return R(L::w(i)) * (R(1) + R(3) * cu + R(4.5) * (cu * cu) - R(1.5) * uu);
+}
+
+// Gamma_i - w_i = w_i { c.u/T + (c.u)^2/(2T^2) - u^2/(2T) }, evaluated directly
+// (the form in which Gamma_i enters g_eq; no cancellation against w_i).
+template <class L, int i, class R>
+__device__ __forceinline__ R gamma_dev_i(const R *u, R uu)
+{
+    const R cu = dot_c<L, i>(u);
+    return R(L::w(i)) * (R(3) * cu + R(4.5) * (cu * cu) - R(1.5) * uu);
+}
+
+// Central-difference gradient and Laplacian (Sec. II, nearest neighbours):
+//   d_a f = sum_i {f(x+c_i) - f(x-c_i)} c_ia w_i / (2T),  lap f = 2 sum_i {f(x+c_i) - f(x)} w_i / T
+// at(i, s) returns f(x + s c_i); mask bit i set <=> x - c_i is solid/outside,
+// where f takes the value fsol.
+template <class L, class R, class At>
+__device__ __forceinline__ void stencil(At &&at, uint32_t mask, R f0, R fsol, R (&grad)[3], R &lap)
+{
+    grad[0] = R(0); grad[1] = R(0); grad[2] = R(0);
+    lap = R(0);
+    static_for<1, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const R fp = ((mask >> opp(i)) & 1u) ? fsol : at(I, 1);
+        const R fm = ((mask >> i) & 1u) ? fsol : at(I, -1);
+        const R d = fp - fm;
+        const R wi = R(L::w(i));
+        static_for<0, 3>([&](auto A) {
+            constexpr int a = decltype(A)::value;
+            if constexpr (L::c(i, a) != 0) acc_c<L::c(i, a)>(grad[a], d * wi);
+        });
+        lap = lap + (fp - f0) * wi;
+    });
+    grad[0] = grad[0] * R(1.5);
+    grad[1] = grad[1] * R(1.5);
+    grad[2] = grad[2] * R(1.5);
+    lap = lap * R(6);
+}
+
+// Moments of one site (S1).  hp, gp: pulled populations; Pn: P^n(x - c_i)
+// (P^n(x) for a solid source); P0 = P^n(x).  Outputs phi, phihat, rho and
+// u^{n+1} (components [0, D)).  Returns kfac = 1/(T rho) and leaves K_i in K.
+template <class L, class R>
+__device__ __forceinline__ void s1_moments(const SiteConsts<R> &k, const R *hp, const R *gp, const R *Pn,
+                                           R P0, R &phi, R &phihat, R &rho, R (&u)[3], R *K)
+{
+    phi = hp[0];
+    static_for<1, L::Q>([&](auto I) { phi = phi + hp[decltype(I)::value]; });
+    phihat = k.clamp ? clamp01(phi) : phi;
+    rho = k.rho_a + phihat * k.drho;
+    const R kfac = R(3) / rho;                          // 1 / (T rho)
+    u[0] = R(0); u[1] = R(0); u[2] = R(0);
+    static_for<0, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        // K_i = w_i / (T rho) { P(x - c_i) - P(x) }   (Eq. Kiterm)
+        K[i] = R(L::w(i)) * kfac * (Pn[i] - P0);
+        if constexpr (i > 0) {
+            const R t = gp[i] + K[i];                   // u = sum_i (g_i + K_i) c_i
+            static_for<0, 3>([&](auto A) {
+                constexpr int a = decltype(A)::value;
+                if constexpr (L::c(i, a) != 0) acc_c<L::c(i, a)>(u[a], t);
+            });
+        }
+    });
+}
+
+// Pressure of one site (S1):
+//   P = rho_ref T sum_i (g_i + (1 + omega) K_i) + omega rho_ref sum_i w_i (c_i . u^n)|_{x - c_i}
+// sum_wcu = sum_i w_i (c_i . u^n(x - c_i)) accumulated by the caller.
+template <class L, class R>
+__device__ __forceinline__ R s1_pressure(const SiteConsts<R> &k, const R *gp, const R *K, R rho, R sum_wcu)
+{
+    // omega = (rho - rho_a) / (rho_w - rho_a) (omega_max - 1)
+    const R omega = (rho - k.rho_a) / k.drho * k.om1;
+    const R op1 = R(1) + omega;
+    R s = gp[0];
+    static_for<1, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        s = s + (gp[i] + op1 * K[i]);
+    });
+    return k.rhoref_T * s + omega * k.rho_a * sum_wcu;
+}
+
+// S3..S5 of one site: from phi, phihat, rho, P = P^{n+1}, u = u^{n+1}, the
+// stencils and the pulled populations (hp, gp), the post-collision
+// populations hs, gs.  INIT: return the equilibria (start state).
+template <class L, class R, bool INIT>
+__device__ __forceinline__ void collide(const SiteConsts<R> &k, R phi, R phihat, R rho, R P, const R (&u)[3],
+                                        const R (&gphi)[3], R lphi, const R (&gu)[3][3], const R *hp,
+                                        const R *gp, R *hs, R *gs)
+{
+    constexpr int D = L::D;
+    // --- S3: normal, theta, delta-theta, chemical potential, force
+    R gg = gphi[0] * gphi[0] + gphi[1] * gphi[1];
+    if constexpr (D == 3) gg = gg + gphi[2] * gphi[2];
+    const R gnorm = sqrt(gg);
+    R n[3];
+    n[0] = gphi[0] / (gnorm + k.eps);
+    n[1] = gphi[1] / (gnorm + k.eps);
+    n[2] = (D == 3) ? gphi[2] / (gnorm + k.eps) : R(0);
+    // theta = (M/T) (1 - 4 (phi - 1/2)^2) / W    (Eq. theta_phai_LBeq)
+    const R theta = k.M3 * ((R(1) - R(4) * (phi - R(0.5)) * (phi - R(0.5))) / k.W);
+    // delta-theta with s = lap / (|lap| + eps)
+    R dtheta;
+    {
+        const R s = lphi / (fabs(lphi) + k.eps);
+        const R Y1 = fmin(fmax(R(0), fmin(R(1), (phi - k.phi_n) / k.D)),
+                          fmax(R(0), fmin(R(1), -(phi - R(1)) / k.D)));
+        const R Y2 = fmin(fmax(R(0), fmin(R(1), phi / k.D)),
+                          fmax(R(0), fmin(R(1), -(phi - k.phi_m) / k.D)));
+        dtheta = k.dt_pref * gnorm * ((R(1) + s) * Y1 + (R(1) - s) * Y2);
+    }
+    const R theta_tot = theta + dtheta;
+    // mu = (48 sigma / W) phi (phi - 1)(phi - 1/2) - (3 sigma W / 2) lap phi
+    const R mu = k.A_mu * phi * (phi - R(1)) * (phi - R(0.5)) - k.B_mu * lphi;
+    R F[3];
+    F[0] = rho * k.g[0] + mu * gphi[0];
+    F[1] = rho * k.g[1] + mu * gphi[1];
+    F[2] = (D == 3) ? rho * k.g[2] + mu * gphi[2] : R(0);
+    // tau_mix (Eq. tau_interpolate), nu = T (tau - 1/2), B = 2/3 (nu - lambda_b) + T/2
+    const R tau = k.tau_a + phihat * k.dtau;
+    const R nu = (tau - R(0.5)) * R(1.0 / 3.0);
+    const R B = R(2.0 / 3.0) * (nu - k.lambda_b) + R(1.0 / 6.0);
+    R div = gu[0][0] + gu[1][1];
+    if constexpr (D == 3) div = div + gu[2][2];
+    // sigma_lm grad_m rho with grad rho = (rho_w - rho_a) grad phi
+    R grho[3];
+    grho[0] = k.drho * gphi[0];
+    grho[1] = k.drho * gphi[1];
+    grho[2] = (D == 3) ? k.drho * gphi[2] : R(0);
+    R sg[3];
+    {
+        const R rnu = rho * nu;
+        const R bulk = rho * R(2.0 / 3.0) * (k.lambda_b - nu) * div;
+        R sig[3][3];
+        static_for<0, D>([&](auto A) {
+            constexpr int a = decltype(A)::value;
+            static_for<0, D>([&](auto Bb) {
+                constexpr int b = decltype(Bb)::value;
+                if constexpr (a == b) sig[a][b] = rnu * (gu[a][b] + gu[b][a]) + bulk;
+                else sig[a][b] = rnu * (gu[a][b] + gu[b][a]);
+            });
+        });
+        static_for<0, D>([&](auto A) {
+            constexpr int l = decltype(A)::value;
+            R t = sig[l][0] * grho[0] + sig[l][1] * grho[1];
+            if constexpr (D == 3) t = t + sig[l][2] * grho[2];
+            sg[l] = t;
+        });
+        if constexpr (D == 2) sg[2] = R(0);
+    }
+    R uu = u[0] * u[0] + u[1] * u[1];
+    if constexpr (D == 3) uu = uu + u[2] * u[2];
+
+    // --- S4: h_eq = phi Gamma_i + theta w_i (c_i . n); BGK with tau_phi
+    static_for<0, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const R heq = phi * gamma_i<L, i>(u, uu) + theta_tot * R(L::w(i)) * dot_c<L, i>(n);
+        if constexpr (INIT) hs[i] = heq;
+        else hs[i] = hp[i] - (hp[i] - heq) * k.inv_tau_phi;
+    });
+
+    // --- S5: g_eq (Eq. BGK_LBeq_hydroeq) and the filter collision
+    const R kF = R(3) / rho;        // 1 / (rho T)
+    const R kS = kF / rho;          // 1 / (rho^2 T)
+    const R bdiv = B * div * R(3);  // B div / T
+    R geq[L::Q];
+    static_for<0, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const R wi = R(L::w(i));
+        R v;
+        if constexpr (i == 0) v = P * k.cP + gamma_dev_i<L, i>(u, uu);
+        else v = gamma_dev_i<L, i>(u, uu);
+        if constexpr (i != 0) v = v + wi * dot_c<L, i>(F) * kF;
+        if constexpr (i == 0) v = v + (wi - R(1)) * bdiv;
+        else v = v + wi * bdiv;
+        if constexpr (i != 0) v = v + wi * dot_c<L, i>(sg) * kS;
+        geq[i] = v;
+    });
+    if constexpr (INIT) {
+        static_for<0, L::Q>([&](auto I) { gs[decltype(I)::value] = geq[decltype(I)::value]; });
+        return;
+    } else {
+        // Pi_ab = sum_k c_ka c_kb (g_k - g_eq_k)
+        R Pi[3][3];
+        static_for<0, D>([&](auto A) {
+            constexpr int a = decltype(A)::value;
+            static_for<a, D>([&](auto Bb) {
+                constexpr int b = decltype(Bb)::value;
+                R acc = R(0);
+                static_for<1, L::Q>([&](auto I) {
+                    constexpr int i = decltype(I)::value;
+                    constexpr int cc = L::c(i, a) * L::c(i, b);
+                    if constexpr (cc != 0) acc_c<cc>(acc, gp[i] - geq[i]);
+                });
+                Pi[a][b] = acc;
+                if constexpr (a != b) Pi[b][a] = acc;
+            });
+        });
+        if (!k.full_trace) {
+            // trace-free part: Pi - (tr Pi / d) delta
+            R tr = Pi[0][0] + Pi[1][1];
+            if constexpr (D == 3) tr = tr + Pi[2][2];
+            const R trd = tr / R(D);
+            static_for<0, D>([&](auto A) {
+                constexpr int a = decltype(A)::value;
+                Pi[a][a] = Pi[a][a] - trd;
+            });
+        }
+        // g*_i = g_eq_i + (1 - 1/tau) w_i/(2T^2) (c_ia c_ib - T delta_ab) Pi_ab
+        const R om = R(1) - R(1) / tau;
+        static_for<0, L::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            R contr = R(0);
+            static_for<0, D>([&](auto A) {
+                constexpr int a = decltype(A)::value;
+                static_for<0, D>([&](auto Bb) {
+                    constexpr int b = decltype(Bb)::value;
+                    constexpr int cc = L::c(i, a) * L::c(i, b);
+                    if constexpr (a == b) {
+                        if constexpr (cc != 0) contr = contr + R(1.0 - 1.0 / 3.0) * Pi[a][b];
+                        else contr = contr - R(1.0 / 3.0) * Pi[a][b];
+                    } else if constexpr (cc != 0) {
+                        acc_c<cc>(contr, Pi[a][b]);
+                    }
+                });
+            });
+            gs[i] = geq[i] + om * (R(L::w(i)) * R(4.5)) * contr;
+        });
+    }
+}
+
+}  // namespace lbm
