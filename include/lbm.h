@@ -184,6 +184,32 @@ int lbm_load_state(lbm_handle h, const void *host_buf, size_t bytes);
  * (algorithmic traffic: both population sets in and out, P and u in and out). */
 int lbm_footprint(lbm_handle h, size_t *device_bytes, size_t *step_bytes);
 
+/* Allocation-free FP64 sums of caller-owned device fields; the paper has no
+ * counterpart (it is a service for callers, not a step of the method).
+ * For callers that cannot allocate device memory where they need the sums:
+ * work being recorded into a CUDA graph by stream capture (cudaMalloc cannot
+ * be captured), real-time loops that must not block in an allocator, and
+ * hosts whose device memory belongs to a pool they do not own.
+ * Inputs: d_phi[n], d_u[3][n] (device doubles, e.g. from
+ * lbm_read_fields_device), d_solid[n] (device bytes, 1 = solid, or NULL),
+ * rho_w > rho_a > 0 and clamp_phi_props as in lbm_params.  Output: d_out[5]
+ * (device doubles) = sum phi, sum rho(phi) u (3 components), fluid sites,
+ * summed over non-solid sites in the same order as lbm_reduce, so with
+ * FP64 storage the two agree bit for bit.  Enqueued on `stream` (a
+ * cudaStream_t, NULL = legacy default); no synchronisation.
+ * No cudaMalloc, cudaFree or allocating library call is made: the per-block
+ * partial sums live in one fixed 40 KB array (1024 blocks x 5 doubles) in
+ * device global memory that every GPU loading this library holds until the
+ * process exits.  Limit: 1 <= n <= 2^31 - 1 sites; larger n (or n <= 0)
+ * returns LBM_ERR_INVALID_ARG.  The first call with a given device current
+ * looks up the array's device address (cudaGetSymbolAddress) and caches it;
+ * make that first call before any stream capture.  All calls share the
+ * array and it keeps the last call's contents (each call overwrites every
+ * partial it reads, so nothing needs clearing); calls that overlap on the
+ * GPU (different streams, or different host threads) race on it. */
+int lbm_reduce_fields_noalloc(const double *d_phi, const double *d_u, const uint8_t *d_solid, int64_t n,
+                              double rho_w, double rho_a, int32_t clamp_phi_props, double *d_out, void *stream);
+
 /* Description of the last error on h (or of the last lbm_create failure when
  * h is NULL).  Never NULL. */
 const char *lbm_last_error(lbm_handle h);

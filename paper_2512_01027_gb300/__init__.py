@@ -84,6 +84,8 @@ SIGNATURES = {
     "lbm_save_state": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     "lbm_load_state": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     "lbm_footprint": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
+    "lbm_reduce_fields_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _i64, ctypes.c_double, ctypes.c_double,
+                                                  ctypes.c_int32, _vp, _vp]),
     "lbm_last_error": (ctypes.c_char_p, [_vp]),
 }
 

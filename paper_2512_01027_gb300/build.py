@@ -24,6 +24,7 @@ UNITS = {
     "lbm_inst_f64.cu": ["--fmad=false"],
     "lbm_inst_f32.cu": [],
     "lbm_inst_f16.cu": [],
+    "lbm_noalloc.cu": [],
 }
 
 
