@@ -1,5 +1,5 @@
 #!/usr/bin/env python
-"""Benchmark of the fused coupled-LB step on GB300.
+"""Benchmark of the coupled-LB step on GB300.
 
 Workload (one step = one time step of the whole lattice through every row of
 the hot path): 3D D3Q27 droplet impact on a liquid film, 256^3 sites, FP32,
@@ -8,8 +8,8 @@ periodic in x and y, solid planes z = 0 and z = 255, droplet R = 32 falling at
 perturbation of phi at the interface.  Inputs are synthetic (workloads/).
 
 Metric: MLUPS (million lattice-site updates per second) of the coupled step,
-the roofline fraction of the step kernel against the measured HBM copy
-bandwidth, an end-to-end MLUPS through the C ABI with host buffers, and the
+the roofline fraction of the step (its algorithmic bytes over its measured
+time, against the measured HBM copy bandwidth), an end-to-end MLUPS through the C ABI with host buffers, and the
 FP64 oracle on the host cores as a CPU baseline.
 
 Launch: python bench.py [--gpus N --steps K --warmup W]; for N > 1 under
@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=256, help="grid edge of the workload")
     ap.add_argument("--storage", default="f32")
+    ap.add_argument("--variant", type=int, default=0,
+                    help="0 automatic (split form), 1 fused plane-synchronous, 2 fused pipelined, 3 split form")
+    ap.add_argument("--inplace", action="store_true", help="one population store, AA streaming")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -199,7 +202,10 @@ def run_ours(args):
     c = workload(args.n)
     prm = {k: v for k, v in c.params.items() if k != "g_ext"}
     L = lbm.Lattice(c.lattice, c.shape, periodic=c.periodic, solid=c.solid, storage=args.storage,
-                    g_ext=c.params["g_ext"], **prm)
+                    g_ext=c.params["g_ext"], inplace=int(args.inplace), **prm)
+    if args.variant:
+        L.set_tuning(args.variant, 0)
+    split = args.inplace or args.variant in (0, 3)
     stream = torch.cuda.current_stream()
     L.set_stream(stream)
     L.init_fields(c.phi0, c.P0, c.u0)
@@ -236,12 +242,12 @@ def run_ours(args):
     try:
         with open(TRAFFIC_FILE) as f:
             tr = json.load(f)
-        if tr.get("source_hash") == kernel_source_hash() and tr.get("n") == args.n and \
-                tr.get("storage") == args.storage:
-            traffic = tr["dram_bytes_per_launch"]
+        key = f"n{args.n}-{args.storage}-{'split' if split else 'v%d' % args.variant}{'-inplace' if args.inplace else ''}"
+        ent = tr.get(key, {})
+        if ent.get("source_hash") == kernel_source_hash():
+            traffic = ent["dram_bytes_per_step"]
     except Exception:
         traffic = None
-
     e2e = None
     if not args.no_e2e:
         # end to end through the C ABI: host fields (pinned) -> device -> K steps -> host fields
@@ -289,10 +295,13 @@ def run_ours(args):
                        "l2": f"inputs larger than L2 ({(L.footprint()[0]) / 1e9:.1f} GB state per lattice)"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
-                         "peak_kind": peak_kind, "kernel": "step_kernel (fused S0..S5, one launch per step)",
+                         "peak_kind": peak_kind,
+                         "kernel": ("moments_kernel + collide_kernel (split form, one step = both launches)"
+                                    if split else "step_kernel (fused S0..S5, one launch per step)"),
+                         "store": "in-place AA" if args.inplace else "ping-pong",
                          "bytes_per_site": per_site},
             "e2e": e2e,
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * (2 if split else 1),
             "clocks": clk,
             "cpu_baseline": cpu,
         }

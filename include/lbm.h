@@ -92,7 +92,9 @@ typedef struct {
     int32_t filter_full_trace; /* 0: filter carries the trace-free part of Pi (default);
                                   1: the full Pi as printed (linearly unstable at low nu) */
     int32_t storage;           /* lbm_storage of the populations (default LBM_STORE_F32) */
-    int32_t reserved;          /* must be 0 */
+    int32_t inplace;           /* 0: two population stores (ping-pong, default); 1: one store
+                                  updated in place with the AA streaming pattern (half the
+                                  population memory; steps run in the two-launch split form) */
 } lbm_params;
 
 /* Fill *p with the paper's defaults: rho_w = 1, rho_a = 1e-3, nu_w = 0.0167,
@@ -168,17 +170,33 @@ int lbm_get_state(lbm_handle h, double *h_pop, double *g_pop, double *P, double 
 
 /* State at n chosen sites (linear indices x + nx (y + ny z)): decoded
  * populations h_pop[n][Q], g_pop[n][Q], P[n] and u[n][3] as doubles, in the
- * library's direction order; any output may be NULL.  For probes (pressure
- * sensors) and for sampled checks of large lattices.  Synchronises. */
+ * library's direction order; any output may be NULL.  Solid sites hold no
+ * state and read as zeros.  For probes (pressure sensors) and for sampled
+ * checks of large lattices.  Synchronises. */
 int lbm_probe(lbm_handle h, int64_t n, const int64_t *sites, double *h_pop, double *g_pop, double *P, double *u);
 
-/* Checkpoint: raw state bytes (populations in storage format, P, u, step
+/* Checkpoint: a 40-byte header (lattice, storage, layout, grid), then the
+ * raw state (populations in storage format and store layout, P, u, step
  * counter).  lbm_state_bytes gives the size; save/load copy through a host
- * buffer of exactly that size.  A state loads into a handle of the same
- * grid, lattice and storage. */
+ * buffer of exactly that size.  A state loads only into a handle of the same
+ * lattice, grid, storage and layout (in-place or not); anything else is
+ * LBM_ERR_INVALID_ARG and leaves the handle unchanged. */
 int lbm_state_bytes(lbm_handle h, size_t *bytes);
 int lbm_save_state(lbm_handle h, void *host_buf, size_t bytes);
 int lbm_load_state(lbm_handle h, const void *host_buf, size_t bytes);
+
+/* Launch tuning of the step (used by the autotuner).  variant: 0 =
+ * automatic (the split form), 1 = fused plane-synchronous kernel, 2 = fused
+ * pipelined kernel (3D lattices with 4-byte populations, else
+ * LBM_ERR_UNSUPPORTED), 3 = split form (two launches per step: moments, then
+ * stencils + collisions).  An in-place handle always uses the split form
+ * (variants 1 and 2 are LBM_ERR_UNSUPPORTED there).  zchunk: z planes per
+ * block of the fused kernels (0 = automatic); it never changes results.
+ * Every variant evaluates the same formulas in the same order: with FP64
+ * storage (built without FMA contraction) all variants agree bit for bit;
+ * with FP32 arithmetic the compiler may contract a product and a sum into
+ * one FMA differently in different kernels, so variants agree to rounding. */
+int lbm_set_tuning(lbm_handle h, int variant, int zchunk);
 
 /* Device bytes held by h, and the bytes one step reads and writes at minimum
  * (algorithmic traffic: both population sets in and out, P and u in and out). */

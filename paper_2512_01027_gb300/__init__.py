@@ -49,7 +49,7 @@ class Params(ctypes.Structure):
         "phi_m", "D", "eps")] + [("g_ext", ctypes.c_double * 3),
                                 ("clamp_phi_props", ctypes.c_int32),
                                 ("filter_full_trace", ctypes.c_int32),
-                                ("storage", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                                ("storage", ctypes.c_int32), ("inplace", ctypes.c_int32)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -83,6 +83,7 @@ SIGNATURES = {
     "lbm_state_bytes": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
     "lbm_save_state": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     "lbm_load_state": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
+    "lbm_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "lbm_footprint": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
     "lbm_reduce_fields_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _i64, ctypes.c_double, ctypes.c_double,
                                                   ctypes.c_int32, _vp, _vp]),
@@ -320,6 +321,11 @@ class Lattice:
     def load_state(self, data: bytes):
         buf = ctypes.create_string_buffer(data, len(data))
         _check(lib().lbm_load_state(self._h, buf, len(data)), self._h)
+
+    def set_tuning(self, variant: int = 0, zchunk: int = 0):
+        """variant 0 auto, 1 fused plane-synchronous, 2 fused pipelined, 3 split form;
+        zchunk 0 = auto."""
+        _check(lib().lbm_set_tuning(self._h, int(variant), int(zchunk)), self._h)
 
     def footprint(self):
         dev = ctypes.c_size_t()

@@ -241,8 +241,8 @@ int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params, lbm_
         return fail(nullptr, LBM_ERR_INVALID_ARG,
                     "invalid parameters (need rho_w > rho_a > 0, nu > 0, M > 0, W > 0, D > 0)");
     const int storage = p.storage;
-    if (storage_bytes(storage) == 0 || p.reserved != 0)
-        return fail(nullptr, LBM_ERR_INVALID_ARG, "unknown storage / reserved != 0");
+    if (storage_bytes(storage) == 0 || (p.inplace != 0 && p.inplace != 1))
+        return fail(nullptr, LBM_ERR_INVALID_ARG, "unknown storage, or inplace not 0/1");
     const Ops *ops = nullptr;
     switch (storage) {
     case LBM_STORE_F64: ops = ops_f64(lattice); break;
@@ -293,13 +293,20 @@ int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params, lbm_
     } else {
         c->zchunk = 1;
     }
+    c->zchunk_auto = c->zchunk;
 
     const size_t sb = storage_bytes(storage), cb = compute_bytes(storage);
     c->pop_bytes = (size_t)Q * (size_t)N * sb;
     c->field_bytes = (size_t)N * cb;
+    c->inplace = p.inplace == 1;
     for (int b = 0; b < 2; ++b) {
-        c->h[b] = own(c, c->pop_bytes);
-        c->g[b] = own(c, c->pop_bytes);
+        if (b == 1 && c->inplace) {
+            c->h[1] = c->h[0];
+            c->g[1] = c->g[0];
+        } else {
+            c->h[b] = own(c, c->pop_bytes);
+            c->g[b] = own(c, c->pop_bytes);
+        }
         c->P[b] = own(c, c->field_bytes);
         c->u[b] = own(c, c->field_bytes * D);
         if (!c->h[b] || !c->g[b] || !c->P[b] || !c->u[b]) {
@@ -308,6 +315,13 @@ int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params, lbm_
             delete c;
             return LBM_ERR_OOM;
         }
+    }
+    c->phi = own(c, c->field_bytes);
+    if (!c->phi) {
+        g_create_err = "device allocation of the phi field failed";
+        release(c);
+        delete c;
+        return LBM_ERR_OOM;
     }
     c->d_err = static_cast<int *>(own(c, 256));
     c->d_scratch = static_cast<double *>(own(c, sizeof(double) * kScratchDoubles));
@@ -319,8 +333,10 @@ int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params, lbm_
     }
     int rc = LBM_OK;
     for (int b = 0; b < 2 && rc == LBM_OK; ++b) {
-        rc = cuda_fail(c, cudaMemset(c->h[b], 0, c->pop_bytes), "cudaMemset");
-        if (rc == LBM_OK) rc = cuda_fail(c, cudaMemset(c->g[b], 0, c->pop_bytes), "cudaMemset");
+        if (!(b == 1 && c->inplace)) {
+            rc = cuda_fail(c, cudaMemset(c->h[b], 0, c->pop_bytes), "cudaMemset");
+            if (rc == LBM_OK) rc = cuda_fail(c, cudaMemset(c->g[b], 0, c->pop_bytes), "cudaMemset");
+        }
         if (rc == LBM_OK) rc = cuda_fail(c, cudaMemset(c->P[b], 0, c->field_bytes), "cudaMemset");
         if (rc == LBM_OK) rc = cuda_fail(c, cudaMemset(c->u[b], 0, c->field_bytes * D), "cudaMemset");
     }
@@ -501,10 +517,32 @@ int lbm_probe(lbm_handle h, int64_t n, const int64_t *sites, double *h_pop, doub
     return rc;
 }
 
+// Checkpoint header: identifies the layout the raw bytes after it are in.
+struct StateHeader {
+    char magic[8];                 // "LBMSTATE"
+    int32_t version, lattice, storage, inplace;
+    int32_t nx, ny, nz, reserved;
+};
+static_assert(sizeof(StateHeader) == 40, "state header layout");
+
+static StateHeader state_header(lbm_handle h)
+{
+    StateHeader s{};
+    std::memcpy(s.magic, "LBMSTATE", 8);
+    s.version = 1;
+    s.lattice = h->lattice;
+    s.storage = h->storage;
+    s.inplace = h->inplace ? 1 : 0;
+    s.nx = h->nx;
+    s.ny = h->ny;
+    s.nz = h->nz;
+    return s;
+}
+
 int lbm_state_bytes(lbm_handle h, size_t *bytes)
 {
     if (!h || !bytes) return LBM_ERR_INVALID_ARG;
-    *bytes = 2 * h->pop_bytes + (size_t)(1 + h->D) * h->field_bytes + sizeof(int64_t);
+    *bytes = sizeof(StateHeader) + 2 * h->pop_bytes + (size_t)(1 + h->D) * h->field_bytes + sizeof(int64_t);
     return LBM_OK;
 }
 
@@ -515,6 +553,9 @@ int lbm_save_state(lbm_handle h, void *host_buf, size_t bytes)
     lbm_state_bytes(h, &need);
     if (bytes != need) return fail(h, LBM_ERR_INVALID_ARG, "buffer size != lbm_state_bytes");
     char *p = static_cast<char *>(host_buf);
+    const StateHeader hd = state_header(h);
+    std::memcpy(p, &hd, sizeof hd);
+    p += sizeof hd;
     const int b = h->cur;
     int rc = cuda_fail(h, cudaMemcpyAsync(p, h->h[b], h->pop_bytes, cudaMemcpyDeviceToHost, h->stream), "D2H state");
     p += h->pop_bytes;
@@ -536,6 +577,10 @@ int lbm_load_state(lbm_handle h, const void *host_buf, size_t bytes)
     lbm_state_bytes(h, &need);
     if (bytes != need) return fail(h, LBM_ERR_INVALID_ARG, "buffer size != lbm_state_bytes");
     const char *p = static_cast<const char *>(host_buf);
+    const StateHeader want = state_header(h);
+    if (std::memcmp(p, &want, sizeof want) != 0)
+        return fail(h, LBM_ERR_INVALID_ARG, "state was saved by a handle of another lattice, grid, storage or layout");
+    p += sizeof want;
     const int b = h->cur;
     int rc = cuda_fail(h, cudaMemcpyAsync(h->h[b], p, h->pop_bytes, cudaMemcpyHostToDevice, h->stream), "H2D state");
     p += h->pop_bytes;
@@ -551,11 +596,25 @@ int lbm_load_state(lbm_handle h, const void *host_buf, size_t bytes)
     return rc;
 }
 
+int lbm_set_tuning(lbm_handle h, int variant, int zchunk)
+{
+    if (!h) return LBM_ERR_INVALID_ARG;
+    if (variant < 0 || variant > 3 || zchunk < 0) return fail(h, LBM_ERR_INVALID_ARG, "variant in 0..3, zchunk >= 0");
+    if (variant == 2 && !h->ops->has_v2())
+        return fail(h, LBM_ERR_UNSUPPORTED, "pipelined kernel needs a 3D lattice with FP32 populations");
+    if (h->inplace && (variant == 1 || variant == 2))
+        return fail(h, LBM_ERR_UNSUPPORTED, "an in-place store streams with the split form only");
+    h->variant = variant;
+    if (h->D == 3) h->zchunk = zchunk > 0 ? (zchunk < h->nz ? zchunk : h->nz) : h->zchunk_auto;
+    return LBM_OK;
+}
+
 int lbm_footprint(lbm_handle h, size_t *device_bytes, size_t *step_bytes)
 {
     if (!h) return LBM_ERR_INVALID_ARG;
     if (device_bytes) {
-        size_t s = 4 * h->pop_bytes + 2 * (size_t)(1 + h->D) * h->field_bytes + sizeof(double) * kScratchDoubles + 256;
+        size_t s = (h->inplace ? 2 : 4) * h->pop_bytes + (3 + 2 * (size_t)h->D) * h->field_bytes +
+                   sizeof(double) * kScratchDoubles + 256;
         if (h->mask) s += sizeof(uint32_t) * (size_t)h->N;
         *device_bytes = s;
     }

@@ -6,6 +6,10 @@
 
 #include "lbm_internal.h"
 #include "lbm_kernels.cuh"
+#include "lbm_step_v2.cuh"
+#include "lbm_split.cuh"
+
+#include <type_traits>
 
 namespace lbm {
 
@@ -29,6 +33,34 @@ struct Impl {
 
     static size_t step_smem() { return step_smem_bytes<L, R>(); }
 
+    static constexpr bool kV2 = (L::D == 3) && sizeof(S) == 4 && std::is_same<R, float>::value;
+    static bool has_v2() { return kV2; }
+
+    template <bool M>
+    static int launch_step_v2(lbm_ctx *c, const StepArgs<R, S> &a)
+    {
+        if constexpr (kV2) {
+            using Tl = TileV2<L>;
+            const size_t smem = step_v2_smem_bytes<L, R, S>();
+            static bool attr_set = false;
+            if (!attr_set) {
+                cudaError_t e = cudaFuncSetAttribute(step_kernel_v2<L, R, C, M>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return cuda_fail(c, e, "cudaFuncSetAttribute(step v2)");
+                attr_set = true;
+            }
+            dim3 block(Tl::SX, Tl::SY, 1);
+            dim3 grid((c->nx + Tl::TX - 1) / Tl::TX, (c->ny + Tl::TY - 1) / Tl::TY,
+                      (c->nz + c->zchunk - 1) / c->zchunk);
+            step_kernel_v2<L, R, C, M><<<grid, block, smem, c->stream>>>(a);
+            return cuda_fail(c, cudaGetLastError(), "step_kernel_v2 launch");
+        } else {
+            (void)a;
+            c->err = "pipelined step kernel not available for this lattice/storage";
+            return LBM_ERR_UNSUPPORTED;
+        }
+    }
+
     template <bool M>
     static int launch_step(lbm_ctx *c, const StepArgs<R, S> &a)
     {
@@ -48,8 +80,53 @@ struct Impl {
         return cuda_fail(c, cudaGetLastError(), "step_kernel launch");
     }
 
+    template <int MODE>
+    static int launch_split(lbm_ctx *c, const SplitArgs<R, S> &a)
+    {
+        const unsigned blocks = (unsigned)((c->N + kSplitThreads - 1) / kSplitThreads);
+        if (c->has_mask) {
+            moments_kernel<L, R, C, true, MODE><<<blocks, kSplitThreads, 0, c->stream>>>(a);
+            collide_kernel<L, R, C, true, MODE><<<blocks, kSplitThreads, 0, c->stream>>>(a);
+        } else {
+            moments_kernel<L, R, C, false, MODE><<<blocks, kSplitThreads, 0, c->stream>>>(a);
+            collide_kernel<L, R, C, false, MODE><<<blocks, kSplitThreads, 0, c->stream>>>(a);
+        }
+        return cuda_fail(c, cudaGetLastError(), "split step launch");
+    }
+
+    static int step_split(lbm_ctx *c, int64_t n)
+    {
+        SplitArgs<R, S> a;
+        a.mask = c->mask;
+        a.err = c->d_err;
+        a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
+        a.N = c->N;
+        a.k = site_consts<R>(c->consts);
+        a.phi = static_cast<R *>(c->phi);
+        for (int64_t s = 0; s < n; ++s) {
+            const int src = c->cur, dst = 1 - c->cur;
+            a.src_h = static_cast<const S *>(c->h[src]);
+            a.src_g = static_cast<const S *>(c->g[src]);
+            a.dst_h = static_cast<S *>(c->h[dst]);
+            a.dst_g = static_cast<S *>(c->g[dst]);
+            a.P_old = static_cast<const R *>(c->P[src]);
+            a.P_new = static_cast<R *>(c->P[dst]);
+            a.u_old = static_cast<const R *>(c->u[src]);
+            a.u_new = static_cast<R *>(c->u[dst]);
+            int rc;
+            if (!c->inplace) rc = launch_split<kPingPong>(c, a);
+            else if (c->steps % 2 == 0) rc = launch_split<kAAOdd>(c, a);
+            else rc = launch_split<kAAEven>(c, a);
+            if (rc != LBM_OK) return rc;
+            c->cur = dst;
+            c->steps += 1;
+        }
+        return LBM_OK;
+    }
+
     static int step(lbm_ctx *c, int64_t n)
     {
+        if (c->inplace || c->variant == 3 || c->variant == 0) return step_split(c, n);
         StepArgs<R, S> a;
         a.mask = c->mask;
         a.err = c->d_err;
@@ -68,7 +145,9 @@ struct Impl {
             a.P_new = static_cast<R *>(c->P[dst]);
             a.u_old = static_cast<const R *>(c->u[src]);
             a.u_new = static_cast<R *>(c->u[dst]);
-            const int rc = c->has_mask ? launch_step<true>(c, a) : launch_step<false>(c, a);
+            const bool v2 = kV2 && c->variant != 1;
+            const int rc = v2 ? (c->has_mask ? launch_step_v2<true>(c, a) : launch_step_v2<false>(c, a))
+                              : (c->has_mask ? launch_step<true>(c, a) : launch_step<false>(c, a));
             if (rc != LBM_OK) return rc;
             c->cur = dst;
             c->steps += 1;
@@ -87,6 +166,7 @@ struct Impl {
         a.mask = c->mask;
         a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
         a.N = c->N;
+        a.aa = c->inplace ? 1 : 0;
         a.k = site_consts<R>(c->consts);
         const int threads = 128;
         const unsigned blocks = (unsigned)((c->N + threads - 1) / threads);
@@ -108,6 +188,8 @@ struct Impl {
         a.phi_out = a.P_out = a.u_out = a.hpop_out = a.gpop_out = nullptr;
         a.N = c->N;
         a.cP = R(c->consts.cP);
+        a.aa = c->inplace ? 1 + (int)(c->steps % 2) : 0;
+        a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
         return a;
     }
 
@@ -162,7 +244,7 @@ struct Impl {
 
     static const Ops *ops()
     {
-        static const Ops o = {&init, &step, &read, &reduce, &pjump, &probe, &step_smem};
+        static const Ops o = {&init, &step, &read, &reduce, &pjump, &probe, &step_smem, &has_v2};
         return &o;
     }
 };

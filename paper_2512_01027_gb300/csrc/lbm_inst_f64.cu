@@ -7,9 +7,9 @@ namespace lbm {
 const Ops *ops_f64(int lattice)
 {
     switch (lattice) {
-    case LBM_D2Q9: return Impl<D2Q9, double, CodecId<double>>::ops();
-    case LBM_D3Q19: return Impl<D3Q19, double, CodecId<double>>::ops();
-    case LBM_D3Q27: return Impl<D3Q27, double, CodecId<double>>::ops();
+    case LBM_D2Q9: return Impl<D2Q9, double, CodecId<double, false>>::ops();
+    case LBM_D3Q19: return Impl<D3Q19, double, CodecId<double, false>>::ops();
+    case LBM_D3Q27: return Impl<D3Q27, double, CodecId<double, false>>::ops();
     default: return nullptr;
     }
 }

@@ -45,6 +45,8 @@ struct lbm_ctx {
     void *g[2] = {nullptr, nullptr};
     void *P[2] = {nullptr, nullptr};
     void *u[2] = {nullptr, nullptr};
+    void *phi = nullptr;           // phi^{n+1} of the split form [N]
+    bool inplace = false;          // one population store, AA streaming
     uint32_t *mask = nullptr;
     int *d_err = nullptr;
     double *d_scratch = nullptr;   // reduction partials + results
@@ -52,6 +54,8 @@ struct lbm_ctx {
     size_t field_bytes = 0;        // one scalar field (N)
     int cur = 0;
     int zchunk = 64;
+    int zchunk_auto = 64;
+    int variant = 0;
     cudaStream_t stream = nullptr;
     int64_t steps = 0;
     std::string err;
@@ -71,6 +75,7 @@ struct Ops {
     int (*pjump)(lbm_ctx *c, const double center[3], double r_in, double r_out, double *d_out4);
     int (*probe)(lbm_ctx *c, const long long *d_sites, int n, double *d_h, double *d_g, double *d_P, double *d_u);
     size_t (*step_smem)();
+    bool (*has_v2)();
 };
 
 const Ops *ops_f64(int lattice);

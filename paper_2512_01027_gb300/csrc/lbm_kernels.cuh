@@ -19,6 +19,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 
@@ -32,19 +33,99 @@ constexpr uint32_t kSolidBit = 1u << 31;
 // ---------------------------------------------------------------------------
 // Storage codecs
 
-// Identity storage (FP64 / FP32): populations stored as computed.
-template <class R>
+// Identity storage (FP64 / FP32): populations stored as computed.  PD: the
+// rest population of g is held as g_0 - P^n/(rho_ref T) (reduced-precision
+// paths, see s1_pressure); view_g restores g_0 for callers reading the state.
+template <class R, bool PD>
 struct CodecId {
     using S = R;
+    static constexpr bool kPdev = PD;
     template <int i>
     __device__ __forceinline__ static R dec_h(S v) { return v; }
     template <int i>
     __device__ __forceinline__ static S enc_h(R v) { return v; }
     template <int i>
-    __device__ __forceinline__ static R dec_g(S v, R /*P_site*/, R /*cP*/) { return v; }
+    __device__ __forceinline__ static R dec_g(S v) { return v; }
     template <int i>
-    __device__ __forceinline__ static S enc_g(R v, R /*P_site*/, R /*cP*/) { return v; }
+    __device__ __forceinline__ static S enc_g(R v) { return v; }
+    template <int i>
+    __device__ __forceinline__ static R view_g(S v, R P, R cP)
+    {
+        if constexpr (PD && i == 0) return v + P * cP;
+        else return v;
+    }
 };
+
+// 16-bit storage of scaled deviations from the lattice weights, FP32
+// arithmetic.  h_i is held as t = 2 h_i / w_i - 1 (bulk heavy phase t = 1,
+// bulk light phase t = -1, both exact); g_i as g_i S / w_i (g_i is already a
+// deviation: g_eq_i = Gamma_i - w_i + ...), with S = 1024 for FP16 to keep
+// small values out of the subnormal range and S = 1 for BF16; the rest
+// population of g is held without its P^n / (rho_ref T) part (kPdev).
+template <class H>
+struct Codec16 {
+    using S = H;
+    static constexpr bool kPdev = true;
+    static constexpr bool kHalf = std::is_same<H, __half>::value;
+    static constexpr float kScale = kHalf ? 1024.0f : 1.0f;
+    __device__ __forceinline__ static float to_f(H v)
+    {
+        if constexpr (kHalf) return __half2float(v);
+        else return __bfloat162float(v);
+    }
+    __device__ __forceinline__ static H from_f(float v)
+    {
+        if constexpr (kHalf) return __float2half_rn(v);
+        else return __float2bfloat16_rn(v);
+    }
+};
+
+template <class L, class H>
+struct CodecDev {
+    using S = H;
+    using B = Codec16<H>;
+    static constexpr bool kPdev = true;
+    template <int i>
+    __device__ __forceinline__ static float dec_h(S v)
+    {
+        constexpr float hw = (float)(L::w(i) * 0.5);
+        return (B::to_f(v) + 1.0f) * hw;
+    }
+    template <int i>
+    __device__ __forceinline__ static S enc_h(float h)
+    {
+        constexpr float iw = (float)(2.0 / L::w(i));
+        return B::from_f(h * iw - 1.0f);
+    }
+    template <int i>
+    __device__ __forceinline__ static float dec_g(S v)
+    {
+        constexpr float ws = (float)(L::w(i) / (double)B::kScale);
+        return B::to_f(v) * ws;
+    }
+    template <int i>
+    __device__ __forceinline__ static S enc_g(float g)
+    {
+        constexpr float sw = (float)((double)B::kScale / L::w(i));
+        return B::from_f(g * sw);
+    }
+    template <int i>
+    __device__ __forceinline__ static float view_g(S v, float P, float cP)
+    {
+        if constexpr (i == 0) return dec_g<0>(v) + P * cP;
+        else return dec_g<i>(v);
+    }
+};
+
+// cp.async helpers (LDGSTS: global -> shared without a register round trip)
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // ---------------------------------------------------------------------------
 // Kernel arguments
@@ -72,6 +153,62 @@ __device__ __forceinline__ int wrapc(int v, int n)
 {
     return v < 0 ? v + n : (v >= n ? v - n : v);
 }
+
+enum StreamMode { kPingPong = 0, kAAEven = 1, kAAOdd = 2 };
+
+template <class R, class S>
+struct SplitArgs {
+    const S *src_h, *src_g;   // populations read (ping-pong source, or the single AA store)
+    S *dst_h, *dst_g;         // populations written (ping-pong destination, or the AA store)
+    const R *P_old, *u_old;   // P^n, u^n [D][N]
+    R *P_new, *u_new;         // P^{n+1}, u^{n+1} [D][N]
+    R *phi;                   // phi^{n+1} [N]
+    const uint32_t *mask;
+    int *err;
+    int nx, ny, nz;
+    long long N;
+    SiteConsts<R> k;
+};
+
+// Site coordinates and wrapped neighbour offsets: site of x + s c with
+// s c in {-1, 0, 1} per axis is xo[1 + sc_x] + yo[1 + sc_y] + zo[1 + sc_z].
+struct Nbr {
+    long long xo[3], yo[3], zo[3];
+    __device__ __forceinline__ Nbr(long long idx, int nx, int ny, int nz)
+    {
+        const int x = (int)(idx % nx);
+        const int y = (int)((idx / nx) % ny);
+        const int z = (int)(idx / ((long long)nx * ny));
+        const long long nxy = (long long)nx * ny;
+        xo[0] = wrapc(x - 1, nx); xo[1] = x; xo[2] = wrapc(x + 1, nx);
+        yo[0] = (long long)wrapc(y - 1, ny) * nx; yo[1] = (long long)y * nx; yo[2] = (long long)wrapc(y + 1, ny) * nx;
+        zo[0] = (long long)wrapc(z - 1, nz) * nxy; zo[1] = (long long)z * nxy; zo[2] = (long long)wrapc(z + 1, nz) * nxy;
+    }
+    // site x + s c_i
+    template <class L, int i>
+    __device__ __forceinline__ long long at(int s) const
+    {
+        constexpr int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+        if (s > 0) return xo[1 + cx] + yo[1 + cy] + zo[1 + cz];
+        return xo[1 - cx] + yo[1 - cy] + zo[1 - cz];
+    }
+};
+
+// Post-collision f*_i(x) location after initialisation / an even AA step
+// (parity 0) or after an odd AA step (parity 1).
+template <class L, int i>
+__device__ __forceinline__ long long aa_state_off(const Nbr &nb, long long idx, long long N, uint32_t m, bool has_mask,
+                                                  int parity)
+{
+    if constexpr (i == 0) {
+        return idx;
+    } else {
+        if (parity == 0) return (long long)opp(i) * N + idx;
+        const bool bb = has_mask && ((m >> opp(i)) & 1u);
+        return bb ? (long long)opp(i) * N + idx : (long long)i * N + nb.at<L, i>(1);
+    }
+}
+
 
 template <class L>
 struct Tile {
@@ -168,7 +305,7 @@ step_kernel(const StepArgs<R, typename C::S> a)
                         constexpr int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
                         if constexpr (i == 0) {
                             hp[0] = C::template dec_h<0>(a.src_h[idx]);
-                            gp[0] = C::template dec_g<0>(a.src_g[idx], P0, a.k.cP);
+                            gp[0] = C::template dec_g<0>(a.src_g[idx]);
                             Pn[0] = P0;
                         } else {
                             const long long src = zo[1 - cz] + yo[1 - cy] + xo[1 - cx];
@@ -176,11 +313,11 @@ step_kernel(const StepArgs<R, typename C::S> a)
                             if (solid_src) {
                                 // halfway bounce-back: h_i(x) = h*_{-i}(x)
                                 hp[i] = C::template dec_h<opp(i)>(a.src_h[(long long)opp(i) * N + idx]);
-                                gp[i] = C::template dec_g<opp(i)>(a.src_g[(long long)opp(i) * N + idx], P0, a.k.cP);
+                                gp[i] = C::template dec_g<opp(i)>(a.src_g[(long long)opp(i) * N + idx]);
                                 Pn[i] = P0;
                             } else {
                                 hp[i] = C::template dec_h<i>(a.src_h[(long long)i * N + src]);
-                                gp[i] = C::template dec_g<i>(a.src_g[(long long)i * N + src], R(0), a.k.cP);
+                                gp[i] = C::template dec_g<i>(a.src_g[(long long)i * N + src]);
                                 Pn[i] = a.P_old[src];
                                 if (interior) {
                                     R un[3];
@@ -195,8 +332,9 @@ step_kernel(const StepArgs<R, typename C::S> a)
                             }
                         }
                     });
-                    R phi, phihat, rho, u[3];
-                    s1_moments<L, R>(a.k, hp, gp, Pn, P0, phi, phihat, rho, u, K);
+                    R phi, phihat, rho, u[3], sumg, sumK;
+                    if constexpr (kPairForms<R>) s1_pairs<L, R>(a.k, hp, gp, Pn, P0, phi, phihat, rho, u, sumg, sumK);
+                    else s1_moments<L, R>(a.k, hp, gp, Pn, P0, phi, phihat, rho, u, K);
                     const int rs = (D == 3) ? (zz + 3) % 3 : 0;
                     ring_phi[rs * PL + ty * SX + tx] = phi;
                     static_for<0, D>([&](auto A) {
@@ -204,7 +342,9 @@ step_kernel(const StepArgs<R, typename C::S> a)
                         ring_u[(rs * D + ax) * PL + ty * SX + tx] = u[ax];
                     });
                     if (interior) {
-                        const R Pnew = s1_pressure<L, R>(a.k, gp, K, rho, sum_wcu);
+                        R Pnew;
+                        if constexpr (kPairForms<R>) Pnew = s1_pressure_pairs<R, C::kPdev>(a.k, rho, sumg, sumK, sum_wcu, P0);
+                        else Pnew = s1_pressure<L, R, C::kPdev>(a.k, gp, K, rho, sum_wcu, P0);
                         const int ss = (D == 3) ? (zz & 1) : 0;
                         static_for<0, Q>([&](auto I) {
                             constexpr int i = decltype(I)::value;
@@ -244,7 +384,7 @@ step_kernel(const StepArgs<R, typename C::S> a)
                 };
                 const R phi = ring_phi[r0 * PL + c0];
                 R gphi[3], lphi;
-                stencil<L, R>([&](auto I, int s) { return ring_at(ring_phi, PL, I, s); }, m, phi, phi, gphi, lphi);
+                stencil_any<L, R>([&](auto I, int s) { return ring_at(ring_phi, PL, I, s); }, m, phi, phi, gphi, lphi);
                 R u[3], gu[3][3];
                 u[2] = R(0);
                 gu[0][2] = gu[1][2] = gu[2][0] = gu[2][1] = gu[2][2] = R(0);
@@ -253,7 +393,7 @@ step_kernel(const StepArgs<R, typename C::S> a)
                     const R *base = ring_u + ax * PL;
                     u[ax] = base[r0 * D * PL + c0];
                     R lap_unused;
-                    stencil<L, R>([&](auto I, int s) { return ring_at(base, D * PL, I, s); }, m, u[ax], R(0),
+                    stencil_any<L, R>([&](auto I, int s) { return ring_at(base, D * PL, I, s); }, m, u[ax], R(0),
                                   gu[ax], lap_unused);
                 });
                 const R P = st_P[ss * TI + ti];
@@ -265,12 +405,12 @@ step_kernel(const StepArgs<R, typename C::S> a)
                     hp[i] = st_h[(ss * Q + i) * TI + ti];
                     gp[i] = st_g[(ss * Q + i) * TI + ti];
                 });
-                collide<L, R, false>(a.k, phi, phihat, rho, P, u, gphi, lphi, gu, hp, gp, hs, gs);
+                collide<L, R, false, C::kPdev>(a.k, phi, phihat, rho, P, u, gphi, lphi, gu, hp, gp, hs, gs);
                 const long long idx = (long long)zc * nx * ny + (long long)ys * nx + xs;
                 static_for<0, Q>([&](auto I) {
                     constexpr int i = decltype(I)::value;
                     a.dst_h[(long long)i * N + idx] = C::template enc_h<i>(hs[i]);
-                    a.dst_g[(long long)i * N + idx] = C::template enc_g<i>(gs[i], P, a.k.cP);
+                    a.dst_g[(long long)i * N + idx] = C::template enc_g<i>(gs[i]);
                 });
                 a.P_new[idx] = P;
                 static_for<0, D>([&](auto A) {
@@ -296,6 +436,7 @@ struct InitArgs {
     const uint32_t *mask;
     int nx, ny, nz;
     long long N;
+    int aa;                        // 1: in-place AA store (f*_i(x) goes to slot -i of x)
     SiteConsts<R> k;
 };
 
@@ -324,7 +465,7 @@ __global__ void __launch_bounds__(128) init_kernel(const InitArgs<R, typename C:
     const R phihat = a.k.clamp ? clamp01(phi) : phi;
     const R rho = a.k.rho_a + phihat * a.k.drho;
     R gphi[3], lphi;
-    stencil<L, R>([&](auto I, int s) { return R(a.phi0[nb(I, s)]); }, m, phi, phi, gphi, lphi);
+    stencil_any<L, R>([&](auto I, int s) { return R(a.phi0[nb(I, s)]); }, m, phi, phi, gphi, lphi);
     R u[3], gu[3][3];
     u[2] = R(0);
     gu[0][2] = gu[1][2] = gu[2][0] = gu[2][1] = gu[2][2] = R(0);
@@ -333,15 +474,16 @@ __global__ void __launch_bounds__(128) init_kernel(const InitArgs<R, typename C:
         const double *f = a.u0 + (long long)ax * a.N;
         u[ax] = R(f[idx]);
         R lap_unused;
-        stencil<L, R>([&](auto I, int s) { return R(f[nb(I, s)]); }, m, u[ax], R(0), gu[ax], lap_unused);
+        stencil_any<L, R>([&](auto I, int s) { return R(f[nb(I, s)]); }, m, u[ax], R(0), gu[ax], lap_unused);
     });
     const R P = R(a.P0[idx]);
     R hs[Q], gs[Q];
-    collide<L, R, true>(a.k, phi, phihat, rho, P, u, gphi, lphi, gu, nullptr, nullptr, hs, gs);
+    collide<L, R, true, C::kPdev>(a.k, phi, phihat, rho, P, u, gphi, lphi, gu, nullptr, nullptr, hs, gs);
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        a.h[(long long)i * a.N + idx] = C::template enc_h<i>(hs[i]);
-        a.g[(long long)i * a.N + idx] = C::template enc_g<i>(gs[i], P, a.k.cP);
+        const long long off = (long long)(a.aa ? opp(i) : i) * a.N + idx;
+        a.h[off] = C::template enc_h<i>(hs[i]);
+        a.g[off] = C::template enc_g<i>(gs[i]);
     });
     a.P[idx] = P;
     static_for<0, D>([&](auto A) {
@@ -362,7 +504,19 @@ struct ReadArgs {
     double *hpop_out, *gpop_out;       // optional decoded populations [Q][N]
     long long N;
     R cP;
+    int aa;                            // 0: ping-pong layout; 1 + parity: in-place AA layout
+    int nx, ny, nz;
 };
+
+// Offset of the post-collision f*_i(x) in the current state.
+template <class L, int i, class RA>
+__device__ __forceinline__ long long state_off(const RA &a, long long idx)
+{
+    if (a.aa == 0) return (long long)i * a.N + idx;
+    const uint32_t m = a.mask ? a.mask[idx] : 0u;
+    const Nbr nb(idx, a.nx, a.ny, L::D == 3 ? a.nz : 1);
+    return aa_state_off<L, i>(nb, idx, a.N, m, a.mask != nullptr, a.aa - 1);
+}
 
 template <class L, class R, class C, bool HAS_MASK>
 __global__ void __launch_bounds__(256) read_kernel(const ReadArgs<R, typename C::S> a)
@@ -379,7 +533,7 @@ __global__ void __launch_bounds__(256) read_kernel(const ReadArgs<R, typename C:
             phi = C::template dec_h<0>(a.h[idx]);
             static_for<1, Q>([&](auto I) {
                 constexpr int i = decltype(I)::value;
-                phi = phi + C::template dec_h<i>(a.h[(long long)i * a.N + idx]);
+                phi = phi + C::template dec_h<i>(a.h[state_off<L, i>(a, idx)]);
             });
         }
         a.phi_out[idx] = (double)phi;
@@ -397,9 +551,9 @@ __global__ void __launch_bounds__(256) read_kernel(const ReadArgs<R, typename C:
         static_for<0, Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
             if (a.hpop_out) a.hpop_out[(long long)i * a.N + idx] =
-                solid ? 0.0 : (double)C::template dec_h<i>(a.h[(long long)i * a.N + idx]);
+                solid ? 0.0 : (double)C::template dec_h<i>(a.h[state_off<L, i>(a, idx)]);
             if (a.gpop_out) a.gpop_out[(long long)i * a.N + idx] =
-                solid ? 0.0 : (double)C::template dec_g<i>(a.g[(long long)i * a.N + idx], P, a.cP);
+                solid ? 0.0 : (double)C::template view_g<i>(a.g[state_off<L, i>(a, idx)], P, a.cP);
         });
     }
 }
@@ -414,6 +568,15 @@ __global__ void __launch_bounds__(128) probe_kernel(const ReadArgs<R, typename C
     if (j >= n) return;
     const long long idx = sites[j];
     if (idx < 0 || idx >= a.N) return;
+    if (a.mask && (a.mask[idx] & kSolidBit)) {     // solid sites hold no state
+        if (P) P[j] = 0.0;
+        for (int ax = 0; ax < 3 && u; ++ax) u[(long long)j * 3 + ax] = 0.0;
+        for (int i = 0; i < Q; ++i) {
+            if (hp) hp[(long long)j * Q + i] = 0.0;
+            if (gp) gp[(long long)j * Q + i] = 0.0;
+        }
+        return;
+    }
     const R Ps = a.P[idx];
     if (P) P[j] = (double)Ps;
     if (u) {
@@ -424,8 +587,8 @@ __global__ void __launch_bounds__(128) probe_kernel(const ReadArgs<R, typename C
     }
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        if (hp) hp[(long long)j * Q + i] = (double)C::template dec_h<i>(a.h[(long long)i * a.N + idx]);
-        if (gp) gp[(long long)j * Q + i] = (double)C::template dec_g<i>(a.g[(long long)i * a.N + idx], Ps, a.cP);
+        if (hp) hp[(long long)j * Q + i] = (double)C::template dec_h<i>(a.h[state_off<L, i>(a, idx)]);
+        if (gp) gp[(long long)j * Q + i] = (double)C::template view_g<i>(a.g[state_off<L, i>(a, idx)], Ps, a.cP);
     });
 }
 
@@ -466,7 +629,7 @@ __global__ void __launch_bounds__(kRedThreads) reduce_kernel(const ReadArgs<R, t
         double phi = 0.0;
         static_for<0, Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
-            phi += (double)C::template dec_h<i>(a.h[(long long)i * a.N + idx]);
+            phi += (double)C::template dec_h<i>(a.h[state_off<L, i>(a, idx)]);
         });
         const double ph = clamp ? fmin(1.0, fmax(0.0, phi)) : phi;
         const double rho = (double)rho_a + ph * (double)drho;

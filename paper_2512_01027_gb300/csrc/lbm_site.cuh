@@ -11,6 +11,8 @@
 // implementations only stay equal when their rounding is identical.
 #pragma once
 
+#include <type_traits>
+
 #include "lbm_lattice.cuh"
 
 namespace lbm {
@@ -122,6 +124,102 @@ __device__ __forceinline__ void stencil(At &&at, uint32_t mask, R f0, R fsol, R 
     lap = lap * R(6);
 }
 
+// ---------------------------------------------------------------------------
+// Pair-summed forms for FP32 arithmetic.  Directions come in pairs (c, -c)
+// at indices (2k-1, 2k); every sum over directions with an odd coefficient
+// (a gradient, a first moment) or an even one (a Laplacian, a second moment)
+// is evaluated once per pair.  Algebraically identical to the canonical
+// forms above, in half the operations; the FP64 path keeps the canonical
+// order (its results must reproduce the oracle bit for bit).
+
+template <class R>
+inline constexpr bool kPairForms = std::is_same<R, float>::value;
+
+// Gradient and Laplacian of the stencil (Sec. II) per pair:
+//   d_a f = (1/T) sum_pairs c_ia w_i {f(x+c_i) - f(x-c_i)}
+//   lap f = (2/T) {sum_pairs w_i (f(x+c_i) + f(x-c_i)) - (1 - w_0) f(x)}
+// MASKED = false: no solid/outside neighbour (mask == 0).
+template <class L, class R, bool MASKED, class At>
+__device__ __forceinline__ void stencil_pairs(At &&at, uint32_t mask, R f0, R fsol, R (&grad)[3], R &lap)
+{
+    grad[0] = R(0); grad[1] = R(0); grad[2] = R(0);
+    R s = R(0);
+    static_for<0, (L::Q - 1) / 2>([&](auto P) {
+        constexpr int i = 2 * decltype(P)::value + 1;
+        const auto I = std::integral_constant<int, i>{};
+        R fp = at(I, 1), fm = at(I, -1);
+        if constexpr (MASKED) {
+            if ((mask >> (i + 1)) & 1u) fp = fsol;   // x + c_i = x - c_{-i}
+            if ((mask >> i) & 1u) fm = fsol;
+        }
+        const R wi = R(L::w(i));
+        const R d = (fp - fm) * wi;
+        static_for<0, 3>([&](auto A) {
+            constexpr int a = decltype(A)::value;
+            if constexpr (L::c(i, a) != 0) acc_c<L::c(i, a)>(grad[a], d);
+        });
+        s = s + (fp + fm) * wi;
+    });
+    grad[0] = grad[0] * R(3);
+    grad[1] = grad[1] * R(3);
+    grad[2] = grad[2] * R(3);
+    lap = (s - R(1.0 - L::w(0)) * f0) * R(6);
+}
+
+// Stencil dispatch: pair-summed for FP32 (with a branch for sites without a
+// solid/outside neighbour), canonical for FP64.
+template <class L, class R, class At>
+__device__ __forceinline__ void stencil_any(At &&at, uint32_t mask, R f0, R fsol, R (&grad)[3], R &lap)
+{
+    if constexpr (kPairForms<R>) {
+        if (mask == 0u) stencil_pairs<L, R, false>(at, mask, f0, fsol, grad, lap);
+        else stencil_pairs<L, R, true>(at, mask, f0, fsol, grad, lap);
+    } else {
+        stencil<L, R>(at, mask, f0, fsol, grad, lap);
+    }
+}
+
+// Moments of one site (S1) per pair.  Outputs phi, phihat, rho, u^{n+1} and
+// the sums the pressure needs: sumg = sum_i g_i, sumK = sum_i K_i.
+// Pn: P^n(x - c_i), already replaced by P^n(x) for a solid source.
+template <class L, class R>
+__device__ __forceinline__ void s1_pairs(const SiteConsts<R> &k, const R *hp, const R *gp, const R *Pn, R P0,
+                                         R &phi, R &phihat, R &rho, R (&u)[3], R &sumg, R &sumK)
+{
+    phi = hp[0];
+    static_for<1, L::Q>([&](auto I) { phi = phi + hp[decltype(I)::value]; });
+    phihat = k.clamp ? clamp01(phi) : phi;
+    rho = k.rho_a + phihat * k.drho;
+    const R kfac = R(3) / rho;                          // 1 / (T rho)
+    u[0] = R(0); u[1] = R(0); u[2] = R(0);
+    sumg = gp[0];
+    R swP = R(0);
+    static_for<0, (L::Q - 1) / 2>([&](auto Pp) {
+        constexpr int i = 2 * decltype(Pp)::value + 1;
+        constexpr int io = i + 1;
+        const R wi = R(L::w(i));
+        // (g_i + K_i) - (g_-i + K_-i), K_i = w_i/(T rho) {P(x-c_i) - P(x)}
+        const R t = (gp[i] - gp[io]) + wi * kfac * (Pn[i] - Pn[io]);
+        static_for<0, 3>([&](auto A) {
+            constexpr int a = decltype(A)::value;
+            if constexpr (L::c(i, a) != 0) acc_c<L::c(i, a)>(u[a], t);
+        });
+        sumg = sumg + (gp[i] + gp[io]);
+        swP = swP + wi * (Pn[i] + Pn[io]);
+    });
+    sumK = kfac * (swP - R(1.0 - L::w(0)) * P0);
+}
+
+// Pressure from the pair sums (same formula as s1_pressure).
+template <class R, bool PDEV>
+__device__ __forceinline__ R s1_pressure_pairs(const SiteConsts<R> &k, R rho, R sumg, R sumK, R sum_wcu, R P0)
+{
+    const R omega = (rho - k.rho_a) / k.drho * k.om1;
+    const R s = sumg + (R(1) + omega) * sumK;
+    if constexpr (PDEV) return P0 + k.rhoref_T * s + omega * k.rho_a * sum_wcu;
+    else return k.rhoref_T * s + omega * k.rho_a * sum_wcu;
+}
+
 // Moments of one site (S1).  hp, gp: pulled populations; Pn: P^n(x - c_i)
 // (P^n(x) for a solid source); P0 = P^n(x).  Outputs phi, phihat, rho and
 // u^{n+1} (components [0, D)).  Returns kfac = 1/(T rho) and leaves K_i in K.
@@ -152,8 +250,13 @@ __device__ __forceinline__ void s1_moments(const SiteConsts<R> &k, const R *hp, 
 // Pressure of one site (S1):
 //   P = rho_ref T sum_i (g_i + (1 + omega) K_i) + omega rho_ref sum_i w_i (c_i . u^n)|_{x - c_i}
 // sum_wcu = sum_i w_i (c_i . u^n(x - c_i)) accumulated by the caller.
-template <class L, class R>
-__device__ __forceinline__ R s1_pressure(const SiteConsts<R> &k, const R *gp, const R *K, R rho, R sum_wcu)
+// PDEV (reduced-precision paths): the rest population is held as
+// g_0 - P^n / (rho_ref T), the part of g_eq_0 other than P^n / (rho_ref T);
+// since rho_ref T * (1 / (rho_ref T)) = 1 the same P is P^n + rho_ref T (...),
+// and P^n is carried exactly instead of through a number 1/(rho_ref T) times
+// larger than P.
+template <class L, class R, bool PDEV>
+__device__ __forceinline__ R s1_pressure(const SiteConsts<R> &k, const R *gp, const R *K, R rho, R sum_wcu, R P0)
 {
     // omega = (rho - rho_a) / (rho_w - rho_a) (omega_max - 1)
     const R omega = (rho - k.rho_a) / k.drho * k.om1;
@@ -163,13 +266,16 @@ __device__ __forceinline__ R s1_pressure(const SiteConsts<R> &k, const R *gp, co
         constexpr int i = decltype(I)::value;
         s = s + (gp[i] + op1 * K[i]);
     });
-    return k.rhoref_T * s + omega * k.rho_a * sum_wcu;
+    if constexpr (PDEV) return P0 + k.rhoref_T * s + omega * k.rho_a * sum_wcu;
+    else return k.rhoref_T * s + omega * k.rho_a * sum_wcu;
 }
 
 // S3..S5 of one site: from phi, phihat, rho, P = P^{n+1}, u = u^{n+1}, the
 // stencils and the pulled populations (hp, gp), the post-collision
 // populations hs, gs.  INIT: return the equilibria (start state).
-template <class L, class R, bool INIT>
+// PDEV: the rest population is produced without its P / (rho_ref T) term
+// (see s1_pressure).
+template <class L, class R, bool INIT, bool PDEV = false>
 __device__ __forceinline__ void collide(const SiteConsts<R> &k, R phi, R phihat, R rho, R P, const R (&u)[3],
                                         const R (&gphi)[3], R lphi, const R (&gu)[3][3], const R *hp,
                                         const R *gp, R *hs, R *gs)
@@ -254,7 +360,7 @@ __device__ __forceinline__ void collide(const SiteConsts<R> &k, R phi, R phihat,
         constexpr int i = decltype(I)::value;
         const R wi = R(L::w(i));
         R v;
-        if constexpr (i == 0) v = P * k.cP + gamma_dev_i<L, i>(u, uu);
+        if constexpr (i == 0 && !PDEV) v = P * k.cP + gamma_dev_i<L, i>(u, uu);
         else v = gamma_dev_i<L, i>(u, uu);
         if constexpr (i != 0) v = v + wi * dot_c<L, i>(F) * kF;
         if constexpr (i == 0) v = v + (wi - R(1)) * bdiv;
@@ -265,6 +371,58 @@ __device__ __forceinline__ void collide(const SiteConsts<R> &k, R phi, R phihat,
     if constexpr (INIT) {
         static_for<0, L::Q>([&](auto I) { gs[decltype(I)::value] = geq[decltype(I)::value]; });
         return;
+    } else if constexpr (kPairForms<R>) {
+        // Pi_ab = sum_k c_ka c_kb (g_k - g_eq_k), per pair (c_ka c_kb is even in c)
+        R ne[(L::Q - 1) / 2];
+        static_for<0, (L::Q - 1) / 2>([&](auto Pp) {
+            constexpr int p = decltype(Pp)::value;
+            ne[p] = (gp[2 * p + 1] - geq[2 * p + 1]) + (gp[2 * p + 2] - geq[2 * p + 2]);
+        });
+        R Pi[3][3];
+        static_for<0, D>([&](auto A) {
+            constexpr int a = decltype(A)::value;
+            static_for<a, D>([&](auto Bb) {
+                constexpr int b = decltype(Bb)::value;
+                R acc = R(0);
+                static_for<0, (L::Q - 1) / 2>([&](auto Pp) {
+                    constexpr int p = decltype(Pp)::value;
+                    constexpr int cc = L::c(2 * p + 1, a) * L::c(2 * p + 1, b);
+                    if constexpr (cc != 0) acc_c<cc>(acc, ne[p]);
+                });
+                Pi[a][b] = acc;
+                if constexpr (a != b) Pi[b][a] = acc;
+            });
+        });
+        R tr = Pi[0][0] + Pi[1][1];
+        if constexpr (D == 3) tr = tr + Pi[2][2];
+        if (!k.full_trace) {
+            const R trd = tr / R(D);
+            static_for<0, D>([&](auto A) {
+                constexpr int a = decltype(A)::value;
+                Pi[a][a] = Pi[a][a] - trd;
+            });
+            tr = R(0);
+        }
+        // (c_ia c_ib - T delta_ab) Pi_ab = c_ia c_ib Pi_ab - T tr Pi, the same for i and -i
+        const R om = R(1) - R(1) / tau;
+        const R base = -R(1.0 / 3.0) * tr;
+        gs[0] = geq[0] + om * (R(L::w(0)) * R(4.5)) * base;
+        static_for<0, (L::Q - 1) / 2>([&](auto Pp) {
+            constexpr int i = 2 * decltype(Pp)::value + 1;
+            R contr = base;
+            static_for<0, D>([&](auto A) {
+                constexpr int a = decltype(A)::value;
+                if constexpr (L::c(i, a) != 0) contr = contr + Pi[a][a];
+                static_for<a + 1, D>([&](auto Bb) {
+                    constexpr int b = decltype(Bb)::value;
+                    constexpr int cc = L::c(i, a) * L::c(i, b);
+                    if constexpr (cc != 0) acc_c<cc>(contr, R(2) * Pi[a][b]);
+                });
+            });
+            const R f = om * (R(L::w(i)) * R(4.5)) * contr;
+            gs[i] = geq[i] + f;
+            gs[i + 1] = geq[i + 1] + f;
+        });
     } else {
         // Pi_ab = sum_k c_ka c_kb (g_k - g_eq_k)
         R Pi[3][3];

@@ -1,0 +1,166 @@
+// Split form of the coupled step: two launches per time step, one thread per
+// site, no shared memory and no block-wide synchronisation.
+//
+//   moments_kernel  (S0, S1): pull both populations, phi = sum h_i, K_i,
+//                   u^{n+1}, P^{n+1}; write phi, u^{n+1}, P^{n+1}.
+//   collide_kernel  (S0, S2..S5): pull both populations again, stencils of
+//                   phi and u^{n+1} read from the fields the first launch
+//                   wrote (L1/L2 hits), both collisions, store.
+//
+// The grid-wide dependency between the moments and their stencils is the
+// launch boundary, so no halo is recomputed; the price is a second read of
+// the populations (704 instead of 464 B per FP32 D3Q27 site update).  The
+// split form also admits in-place streaming: with the AA pattern a site
+// reads and writes one and the same set of population slots in every step,
+// so both launches can work on a single population store.
+//
+// Population addressing (slot i of site x is pop[i * N + x]):
+//   ping-pong   read  f_i(x) = src[i][x - c_i]                write dst[i][x]
+//   AA, even    read  f_i(x) = pop[i][x]                      write pop[-i][x]
+//   AA, odd     read  f_i(x) = pop[-i][x - c_i]               write pop[i][x + c_i]
+// with halfway bounce-back: a solid source x - c_i reads the site's own
+// post-collision value of -i (ping-pong: src[-i][x]; AA odd: pop[i][x]); a
+// solid destination x + c_i in an odd step stores to pop[-i][x].  After an
+// even step (and after initialisation) the post-collision f*_i(x) sits in
+// pop[-i][x]; after an odd step in pop[i][x + c_i] (pop[-i][x] next to a
+// solid).
+#pragma once
+
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+// Offset (slot * N + site) from which f_i(x) is read, for the stream mode.
+template <class L, int MODE, int i>
+__device__ __forceinline__ long long read_off(const Nbr &nb, long long idx, long long N, uint32_t m, bool has_mask)
+{
+    if constexpr (i == 0) {
+        return idx;                                   // rest population never moves
+    } else {
+        const bool bb = has_mask && ((m >> i) & 1u);  // x - c_i solid/outside
+        if constexpr (MODE == kPingPong) return bb ? (long long)opp(i) * N + idx : (long long)i * N + nb.at<L, i>(-1);
+        else if constexpr (MODE == kAAEven) return (long long)i * N + idx;
+        else return bb ? (long long)i * N + idx : (long long)opp(i) * N + nb.at<L, i>(-1);
+    }
+}
+
+// Offset to which f*_i(x) is written, for the stream mode.
+template <class L, int MODE, int i>
+__device__ __forceinline__ long long write_off(const Nbr &nb, long long idx, long long N, uint32_t m, bool has_mask)
+{
+    if constexpr (i == 0) {
+        return idx;
+    } else if constexpr (MODE == kPingPong) {
+        return (long long)i * N + idx;
+    } else if constexpr (MODE == kAAEven) {
+        return (long long)opp(i) * N + idx;
+    } else {
+        const bool bb = has_mask && ((m >> opp(i)) & 1u);   // x + c_i solid/outside
+        return bb ? (long long)opp(i) * N + idx : (long long)i * N + nb.at<L, i>(1);
+    }
+}
+
+constexpr int kSplitThreads = 128;
+
+template <class L, class R, class C, bool HAS_MASK, int MODE>
+__global__ void __launch_bounds__(kSplitThreads) moments_kernel(const SplitArgs<R, typename C::S> a)
+{
+    constexpr int D = L::D, Q = L::Q;
+    const long long idx = (long long)blockIdx.x * kSplitThreads + threadIdx.x;
+    if (idx >= a.N) return;
+    uint32_t m = 0;
+    if constexpr (HAS_MASK) m = a.mask[idx];
+    if (m & kSolidBit) return;
+    const long long N = a.N;
+    const Nbr nb(idx, a.nx, a.ny, D == 3 ? a.nz : 1);
+    R hp[Q], gp[Q], Pn[Q], K[Q];
+    const R P0 = a.P_old[idx];
+    R sum_wcu = R(0);
+    static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const long long off = read_off<L, MODE, i>(nb, idx, N, m, HAS_MASK);
+        hp[i] = C::template dec_h<i>(a.src_h[off]);
+        gp[i] = C::template dec_g<i>(a.src_g[off]);
+        if constexpr (i == 0) {
+            Pn[0] = P0;
+        } else {
+            const bool bb = HAS_MASK && ((m >> i) & 1u);
+            const long long src = nb.at<L, i>(-1);
+            Pn[i] = bb ? P0 : a.P_old[src];
+            if (!bb) {
+                R un[3];
+                static_for<0, 3>([&](auto A) {
+                    constexpr int ax = decltype(A)::value;
+                    if constexpr (ax < D && L::c(i, ax) != 0) un[ax] = a.u_old[(long long)ax * N + src];
+                    else un[ax] = R(0);
+                });
+                sum_wcu = sum_wcu + R(L::w(i)) * dot_c<L, i>(un);
+            }
+        }
+    });
+    R phi, phihat, rho, u[3], sumg, sumK;
+    R Pnew;
+    if constexpr (kPairForms<R>) {
+        s1_pairs<L, R>(a.k, hp, gp, Pn, P0, phi, phihat, rho, u, sumg, sumK);
+        Pnew = s1_pressure_pairs<R, C::kPdev>(a.k, rho, sumg, sumK, sum_wcu, P0);
+    } else {
+        s1_moments<L, R>(a.k, hp, gp, Pn, P0, phi, phihat, rho, u, K);
+        Pnew = s1_pressure<L, R, C::kPdev>(a.k, gp, K, rho, sum_wcu, P0);
+    }
+    a.phi[idx] = phi;
+    a.P_new[idx] = Pnew;
+    static_for<0, D>([&](auto A) {
+        constexpr int ax = decltype(A)::value;
+        a.u_new[(long long)ax * N + idx] = u[ax];
+    });
+}
+
+template <class L, class R, class C, bool HAS_MASK, int MODE>
+__global__ void __launch_bounds__(kSplitThreads) collide_kernel(const SplitArgs<R, typename C::S> a)
+{
+    constexpr int D = L::D, Q = L::Q;
+    const long long idx = (long long)blockIdx.x * kSplitThreads + threadIdx.x;
+    if (idx >= a.N) return;
+    uint32_t m = 0;
+    if constexpr (HAS_MASK) m = a.mask[idx];
+    if (m & kSolidBit) return;
+    const long long N = a.N;
+    const Nbr nb(idx, a.nx, a.ny, D == 3 ? a.nz : 1);
+    // S2: stencils of phi^{n+1} and u^{n+1} from the fields of the moments launch
+    const R phi = a.phi[idx];
+    R gphi[3], lphi;
+    stencil_any<L, R>([&](auto I, int s) { return a.phi[nb.at<L, decltype(I)::value>(s)]; }, m, phi, phi, gphi,
+                      lphi);
+    R u[3], gu[3][3];
+    u[2] = R(0);
+    gu[0][2] = gu[1][2] = gu[2][0] = gu[2][1] = gu[2][2] = R(0);
+    static_for<0, D>([&](auto A) {
+        constexpr int ax = decltype(A)::value;
+        const R *f = a.u_new + (long long)ax * N;
+        u[ax] = f[idx];
+        R lap_unused;
+        stencil_any<L, R>([&](auto I, int s) { return f[nb.at<L, decltype(I)::value>(s)]; }, m, u[ax], R(0),
+                          gu[ax], lap_unused);
+    });
+    const R phihat = a.k.clamp ? clamp01(phi) : phi;
+    const R rho = a.k.rho_a + phihat * a.k.drho;
+    const R P = a.P_new[idx];
+    R hp[Q], gp[Q], hs[Q], gs[Q];
+    static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const long long off = read_off<L, MODE, i>(nb, idx, N, m, HAS_MASK);
+        hp[i] = C::template dec_h<i>(a.src_h[off]);
+        gp[i] = C::template dec_g<i>(a.src_g[off]);
+    });
+    collide<L, R, false, C::kPdev>(a.k, phi, phihat, rho, P, u, gphi, lphi, gu, hp, gp, hs, gs);
+    static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const long long off = write_off<L, MODE, i>(nb, idx, N, m, HAS_MASK);
+        a.dst_h[off] = C::template enc_h<i>(hs[i]);
+        a.dst_g[off] = C::template enc_g<i>(gs[i]);
+    });
+    if (!(isfinite(phi) && isfinite(P) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2])))
+        atomicOr(a.err, 1);
+}
+
+}  // namespace lbm
