@@ -53,6 +53,8 @@ def parse():
                     help="0 automatic (split form), 1 fused plane-synchronous, 2 fused pipelined, 3 split form")
     ap.add_argument("--inplace", action="store_true", help="one population store, AA streaming")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -159,6 +161,30 @@ def cpu_baseline(reps_target_s: float = 10.0):
     dt = time.perf_counter() - t0
     return {"value": c.N * steps / dt / 1e6, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": f"FP64 C oracle, D3Q27 droplet on film 64^3 (R = 8), {steps} steps, {dt:.1f} s"}
+
+
+def serving(n_requests: int):
+    """Served solves/s and p50/p99 latency on a bounded sample of the serving
+    workload: oscillating ellipsoidal droplets in periodic boxes of edge
+    {32, 48, 64, 96, 128}, density ratio 10..1000, sigma 5e-4..2e-3, FP32
+    arithmetic with FP16 storage, in-place stores; steps drawn from 50..500
+    (the full workload's 500..5000, scaled by 1/10 to bound the run).
+    1) closed loop: all requests at t = 0 -> capacity (solves/s);
+    2) open loop: Poisson arrivals at 0.8 x capacity -> p50/p99 latency;
+    3) the same open-loop trace one request at a time (FP32, split form)."""
+    from paper_2512_01027_gb300.serving import Server, run_one_at_a_time
+
+    closed = W.request_trace(n=n_requests, rate=1e9, steps_range=(50, 500))
+    srv = Server("D3Q27", "f16", inplace=True, chunk=16)
+    cl = srv.run(closed).summary()
+    cap = cl["solves_per_s"]
+    rate = 0.8 * cap
+    opened = W.request_trace(n=n_requests, rate=rate, steps_range=(50, 500))
+    op = srv.run(opened).summary()
+    srv.close()
+    seq = run_one_at_a_time(opened, storage="f32").summary()
+    return {"workload": f"{n_requests} requests, D3Q27 droplets, edges 32..128, 50..500 steps, f16 storage",
+            "closed_loop": cl, "open_loop": dict(op, arrival_rate_per_s=rate), "one_at_a_time_f32": seq}
 
 
 def dist_init():
@@ -278,6 +304,14 @@ def run_ours(args):
                "h2d_bytes_per_step": int(5 * 8 * N / ke), "d2h_bytes_per_step": int(5 * 8 * N / ke),
                "solve": f"init_fields from pinned host fields, {ke} steps, read_fields to pinned host"}
 
+    state_gb = L.footprint()[0] / 1e9
+    serve = None
+    if not args.no_serve:
+        L.close()
+        del L
+        torch.cuda.empty_cache()
+        serve = serving(args.serve_requests)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
@@ -292,7 +326,7 @@ def run_ours(args):
             "config": {"workload": f"D3Q27 droplet impact on a liquid film, {args.n}^3, {args.storage} storage",
                        "lattice": "D3Q27", "grid": [args.n] * 3, "storage": args.storage,
                        "parallelism": f"replicas x{world}",
-                       "l2": f"inputs larger than L2 ({(L.footprint()[0]) / 1e9:.1f} GB state per lattice)"},
+                       "l2": f"inputs larger than L2 ({state_gb:.1f} GB state per lattice)"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "peak_kind": peak_kind,
@@ -304,6 +338,7 @@ def run_ours(args):
             "gpu_launches": args.steps * (2 if split else 1),
             "clocks": clk,
             "cpu_baseline": cpu,
+            "serving": serve,
         }
         print(json.dumps(line), flush=True)
 

@@ -202,6 +202,12 @@ int lbm_set_tuning(lbm_handle h, int variant, int zchunk);
  * (algorithmic traffic: both population sets in and out, P and u in and out). */
 int lbm_footprint(lbm_handle h, size_t *device_bytes, size_t *step_bytes);
 
+/* Device bytes lbm_create would hold for (grid, lattice, params), computed
+ * on the host without a device and without allocating: for admission
+ * control (a server admits a lattice when its footprint fits in free HBM).
+ * Equals lbm_footprint's device_bytes of the created handle. */
+int lbm_estimate_footprint(const lbm_grid *grid, int lattice, const lbm_params *params, size_t *device_bytes);
+
 /* Allocation-free FP64 sums of caller-owned device fields; the paper has no
  * counterpart (it is a service for callers, not a step of the method).
  * For callers that cannot allocate device memory where they need the sums:
@@ -231,6 +237,74 @@ int lbm_reduce_fields_noalloc(const double *d_phi, const double *d_u, const uint
 /* Description of the last error on h (or of the last lbm_create failure when
  * h is NULL).  Never NULL. */
 const char *lbm_last_error(lbm_handle h);
+
+/* ------------------------------------------------------------------------
+ * Autotuner.  Times `trial_steps` steps of every launch form the handle
+ * supports (split form; fused plane-synchronous kernel; fused pipelined
+ * kernel at several z-chunks where available) on the handle's own state,
+ * keeps the fastest with lbm_set_tuning and restores the state it started
+ * from (through a host copy of lbm_state_bytes bytes), so the results of the
+ * following steps are those of the chosen variant from the same state.
+ * Outputs (any may be NULL): the chosen variant and zchunk and its measured
+ * milliseconds per step.  An in-place handle has one form and returns it
+ * without timing.  Synchronises; 1 <= trial_steps <= 1000. */
+int lbm_autotune(lbm_handle h, int trial_steps, int *variant, int *zchunk, double *ms_per_step);
+
+/* ------------------------------------------------------------------------
+ * Batches: many independent lattices advanced together, two kernel launches
+ * per time step for the whole set (no per-lattice launches), on a
+ * persistent grid.  Work items are blocks of consecutive sites of one
+ * member; a device table lists the members, so one CUDA graph of `chunk`
+ * steps, captured once, serves any membership.  Members are ordinary
+ * handles (their own grid, parameters, walls, storage layout and state),
+ * created with lbm_create and initialised as usual, all of the batch's
+ * lattice and storage.  Each member carries a step budget; a batch step
+ * advances every member by min(n, its remaining budget).  The per-site
+ * arithmetic is the split form's, so a member's results do not depend on
+ * which other lattices share the batch.
+ *
+ * While in a batch, lbm_step on the member returns LBM_ERR_INVALID_ARG;
+ * reading, probing, reductions and checkpoints work as usual (call them
+ * between batch steps).  lbm_destroy of a member removes it from its batch. */
+typedef struct lbm_batch_ctx *lbm_batch;
+
+/* A batch for lattices of one DdQq and storage, on the current device, with
+ * its own non-blocking stream. */
+int lbm_batch_create(int lattice, int storage, lbm_batch *out);
+
+/* Detaches every member (the handles stay valid) and frees the batch. */
+int lbm_batch_destroy(lbm_batch b);
+
+/* Stream of the batch's work (a cudaStream_t, not the legacy default
+ * stream: graphs need a capturable stream).  NULL restores the own stream. */
+int lbm_batch_set_stream(lbm_batch b, void *stream);
+
+/* chunk: steps per graph launch, 1..64 (default 16); use_graph: 0 launches
+ * the kernels one by one (same results). */
+int lbm_batch_set_tuning(lbm_batch b, int chunk, int use_graph);
+
+/* Adds h with a budget of `steps` steps (>= 0).  h must match the batch's
+ * lattice and storage and belong to no other batch (else
+ * LBM_ERR_INVALID_ARG); members index their populations in 32 bits, so
+ * Q x sites must stay below 2^32 (else LBM_ERR_UNSUPPORTED). */
+int lbm_batch_add(lbm_batch b, lbm_handle h, int64_t steps);
+
+/* Removes h (its state stays as the last completed step left it). */
+int lbm_batch_remove(lbm_batch b, lbm_handle h);
+
+/* Advances every member by min(n, remaining budget) steps (n >= 0), chunk by
+ * chunk, and returns when the GPU work is done.  *finished (may be NULL):
+ * members whose budget is now 0. */
+int lbm_batch_step(lbm_batch b, int64_t n, int *finished);
+
+/* Remaining budget of member h. */
+int lbm_batch_remaining(lbm_batch b, lbm_handle h, int64_t *steps_left);
+
+/* Members and kernel launches issued so far (either may be NULL). */
+int lbm_batch_info(lbm_batch b, int *members, int64_t *launches);
+
+/* Description of the batch's last error.  Never NULL. */
+const char *lbm_batch_last_error(lbm_batch b);
 
 #ifdef __cplusplus
 }

@@ -20,7 +20,7 @@ import numpy as np
 
 from . import build as _build
 
-__all__ = ["Lattice", "lib", "build", "default_params", "lattice_info", "LbmError",
+__all__ = ["Lattice", "Batch", "estimate_footprint", "lib", "build", "default_params", "lattice_info", "LbmError",
            "D2Q9", "D3Q19", "D3Q27", "F64", "F32", "F16DEV", "BF16DEV"]
 
 D2Q9, D3Q19, D3Q27 = 0, 1, 2
@@ -88,6 +88,20 @@ SIGNATURES = {
     "lbm_reduce_fields_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _i64, ctypes.c_double, ctypes.c_double,
                                                   ctypes.c_int32, _vp, _vp]),
     "lbm_last_error": (ctypes.c_char_p, [_vp]),
+    "lbm_estimate_footprint": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_int, ctypes.POINTER(Params),
+                                              ctypes.POINTER(ctypes.c_size_t)]),
+    "lbm_autotune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    _dp]),
+    "lbm_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(_vp)]),
+    "lbm_batch_destroy": (ctypes.c_int, [_vp]),
+    "lbm_batch_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "lbm_batch_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "lbm_batch_add": (ctypes.c_int, [_vp, _vp, _i64]),
+    "lbm_batch_remove": (ctypes.c_int, [_vp, _vp]),
+    "lbm_batch_step": (ctypes.c_int, [_vp, _i64, ctypes.POINTER(ctypes.c_int)]),
+    "lbm_batch_remaining": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_i64)]),
+    "lbm_batch_info": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_i64)]),
+    "lbm_batch_last_error": (ctypes.c_char_p, [_vp]),
 }
 
 
@@ -147,6 +161,25 @@ def lattice_info(lattice):
 
 
 _torch_hooks = None
+
+
+def estimate_footprint(lattice, shape, periodic=(1, 1, 1), solid=None, storage="f32", inplace=0) -> int:
+    """Device bytes a Lattice of this description would hold (no device
+    needed, nothing allocated)."""
+    nx, ny, nz = (tuple(shape) + (1, 1))[:3]
+    g = Grid()
+    g.nx, g.ny, g.nz = nx, ny, nz
+    for a in range(3):
+        g.periodic[a] = int(periodic[a])
+    keep = None
+    if solid is not None:
+        keep = np.ascontiguousarray(np.asarray(solid, dtype=np.uint8).reshape(-1))
+        g.solid = keep.ctypes.data
+    p = default_params(storage=storage, inplace=int(inplace))
+    out = ctypes.c_size_t()
+    _check(lib().lbm_estimate_footprint(ctypes.byref(g), LATTICES.get(lattice, lattice), ctypes.byref(p),
+                                        ctypes.byref(out)))
+    return out.value
 
 
 def use_torch_allocator(enable: bool = True) -> None:
@@ -327,8 +360,80 @@ class Lattice:
         zchunk 0 = auto."""
         _check(lib().lbm_set_tuning(self._h, int(variant), int(zchunk)), self._h)
 
+    def autotune(self, trial_steps: int = 5):
+        """Time every launch form on this lattice's state, keep the fastest,
+        restore the state.  Returns (variant, zchunk, ms_per_step)."""
+        v, z, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(lib().lbm_autotune(self._h, int(trial_steps), ctypes.byref(v), ctypes.byref(z), ctypes.byref(ms)),
+               self._h)
+        return v.value, z.value, ms.value
+
     def footprint(self):
         dev = ctypes.c_size_t()
         step = ctypes.c_size_t()
         _check(lib().lbm_footprint(self._h, ctypes.byref(dev), ctypes.byref(step)), self._h)
         return dev.value, step.value
+
+
+def _bcheck(rc, b):
+    if rc != LBM_OK:
+        msg = lib().lbm_batch_last_error(b)
+        raise LbmError(rc, msg.decode() if msg else "")
+
+
+class Batch:
+    """Lattices of one DdQq and storage stepped together: two kernel launches
+    per time step for the whole set, chunks of steps replayed as CUDA graphs.
+    Members are Lattice objects with a step budget each."""
+
+    def __init__(self, lattice="D3Q27", storage="f32"):
+        self._b = _vp()
+        self.members = []
+        _check(lib().lbm_batch_create(LATTICES.get(lattice, lattice), STORAGES.get(storage, storage),
+                                      ctypes.byref(self._b)))
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib().lbm_batch_destroy(self._b)
+            self._b = None
+            self.members = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream=None):
+        ptr = None
+        if stream is not None:
+            ptr = stream if isinstance(stream, int) else stream.cuda_stream
+        _bcheck(lib().lbm_batch_set_stream(self._b, ptr), self._b)
+
+    def set_tuning(self, chunk: int = 16, use_graph: bool = True):
+        _bcheck(lib().lbm_batch_set_tuning(self._b, int(chunk), int(bool(use_graph))), self._b)
+
+    def add(self, lat: "Lattice", steps: int):
+        _bcheck(lib().lbm_batch_add(self._b, lat.handle, int(steps)), self._b)
+        self.members.append(lat)
+
+    def remove(self, lat: "Lattice"):
+        _bcheck(lib().lbm_batch_remove(self._b, lat.handle), self._b)
+        self.members.remove(lat)
+
+    def step(self, n: int) -> int:
+        """Advance every member by min(n, its remaining budget); returns the
+        number of members whose budget is spent."""
+        f = ctypes.c_int()
+        _bcheck(lib().lbm_batch_step(self._b, int(n), ctypes.byref(f)), self._b)
+        return f.value
+
+    def remaining(self, lat: "Lattice") -> int:
+        r = _i64()
+        _bcheck(lib().lbm_batch_remaining(self._b, lat.handle, ctypes.byref(r)), self._b)
+        return r.value
+
+    def info(self):
+        m, n = ctypes.c_int(), _i64()
+        _bcheck(lib().lbm_batch_info(self._b, ctypes.byref(m), ctypes.byref(n)), self._b)
+        return m.value, n.value

@@ -19,13 +19,17 @@ LIB = os.path.join(BUILD, "liblbm_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
           "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-Xcompiler", "-fno-fast-math"]
-UNITS = {
-    "lbm_api.cu": [],
-    "lbm_inst_f64.cu": ["--fmad=false"],
-    "lbm_inst_f32.cu": [],
-    "lbm_inst_f16.cu": [],
-    "lbm_noalloc.cu": [],
-}
+# (source, extra flags, object name): the instantiation units compile once
+# per lattice (and 16-bit type), so the jobs run in parallel.
+UNITS = [("lbm_api.cu", [], "lbm_api.o"),
+         ("lbm_noalloc.cu", [], "lbm_noalloc.o"),
+         ("lbm_batch_api.cu", [], "lbm_batch_api.o")]
+for _lat in range(3):
+    UNITS.append(("lbm_inst_f64.cu", ["--fmad=false", f"-DLBM_LAT={_lat}"], f"lbm_inst_f64_{_lat}.o"))
+    UNITS.append(("lbm_inst_f32.cu", [f"-DLBM_LAT={_lat}"], f"lbm_inst_f32_{_lat}.o"))
+    for _bf in range(2):
+        UNITS.append(("lbm_inst_f16.cu", [f"-DLBM_LAT={_lat}", f"-DLBM_BF16={_bf}"],
+                      f"lbm_inst_{'bf16' if _bf else 'f16'}_{_lat}.o"))
 
 
 def nvcc() -> str:
@@ -50,8 +54,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     cc = nvcc()
 
     def compile_unit(item):
-        src, extra = item
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        src, extra, oname = item
+        obj = os.path.join(BUILD, oname)
         cmd = [cc, *ARCH, *COMMON, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if ptxas_info:
             cmd.insert(1, "-Xptxas=-v")
@@ -60,8 +64,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")
         return obj, r.stderr
 
-    with ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
-        results = list(ex.map(compile_unit, UNITS.items()))
+    with ThreadPoolExecutor(max_workers=min(len(UNITS), max(2, os.cpu_count() or 2))) as ex:
+        results = list(ex.map(compile_unit, UNITS))
     if verbose or ptxas_info:
         for obj, err in results:
             if err:

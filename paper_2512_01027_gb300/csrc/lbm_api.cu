@@ -127,6 +127,17 @@ size_t storage_bytes(int storage)
 
 size_t compute_bytes(int storage) { return storage == LBM_STORE_F64 ? 8 : 4; }
 
+// Device bytes of a handle: population sets, P and u (two each), phi,
+// reduction scratch, error flag, and the neighbour mask when there is one.
+size_t footprint_bytes(int Q, int D, long long N, int storage, bool inplace, bool has_mask)
+{
+    const size_t pop = (size_t)Q * (size_t)N * storage_bytes(storage);
+    const size_t field = (size_t)N * compute_bytes(storage);
+    size_t s = (inplace ? 2 : 4) * pop + (3 + 2 * (size_t)D) * field + sizeof(double) * kScratchDoubles + 256;
+    if (has_mask) s += sizeof(uint32_t) * (size_t)N;
+    return s;
+}
+
 void release(lbm_ctx *c)
 {
     if (c->stream) cudaStreamSynchronize(c->stream);
@@ -243,13 +254,7 @@ int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params, lbm_
     const int storage = p.storage;
     if (storage_bytes(storage) == 0 || (p.inplace != 0 && p.inplace != 1))
         return fail(nullptr, LBM_ERR_INVALID_ARG, "unknown storage, or inplace not 0/1");
-    const Ops *ops = nullptr;
-    switch (storage) {
-    case LBM_STORE_F64: ops = ops_f64(lattice); break;
-    case LBM_STORE_F32: ops = ops_f32(lattice); break;
-    case LBM_STORE_F16DEV: ops = ops_f16(lattice); break;
-    case LBM_STORE_BF16DEV: ops = ops_bf16(lattice); break;
-    }
+    const Ops *ops = ops_for(lattice, storage);
     if (!ops) return fail(nullptr, LBM_ERR_UNSUPPORTED, "lattice/storage combination not built");
 
     int ndev = 0;
@@ -376,6 +381,7 @@ int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params, lbm_
 int lbm_destroy(lbm_handle h)
 {
     if (!h) return LBM_ERR_INVALID_ARG;
+    if (h->batch) lbm_batch_remove(h->batch, h);
     release(h);
     delete h;
     return LBM_OK;
@@ -415,6 +421,7 @@ int lbm_step(lbm_handle h, int64_t n)
 {
     if (!h) return LBM_ERR_INVALID_ARG;
     if (n < 0) return fail(h, LBM_ERR_INVALID_ARG, "n < 0");
+    if (h->batch) return fail(h, LBM_ERR_INVALID_ARG, "the handle is stepped by its batch (lbm_batch_step)");
     return h->ops->step(h, n);
 }
 
@@ -612,13 +619,23 @@ int lbm_set_tuning(lbm_handle h, int variant, int zchunk)
 int lbm_footprint(lbm_handle h, size_t *device_bytes, size_t *step_bytes)
 {
     if (!h) return LBM_ERR_INVALID_ARG;
-    if (device_bytes) {
-        size_t s = (h->inplace ? 2 : 4) * h->pop_bytes + (3 + 2 * (size_t)h->D) * h->field_bytes +
-                   sizeof(double) * kScratchDoubles + 256;
-        if (h->mask) s += sizeof(uint32_t) * (size_t)h->N;
-        *device_bytes = s;
-    }
+    if (device_bytes) *device_bytes = footprint_bytes(h->Q, h->D, h->N, h->storage, h->inplace, h->mask != nullptr);
     if (step_bytes) *step_bytes = 2 * (2 * h->pop_bytes) + 2 * (size_t)(1 + h->D) * h->field_bytes;
+    return LBM_OK;
+}
+
+int lbm_estimate_footprint(const lbm_grid *grid, int lattice, const lbm_params *params, size_t *device_bytes)
+{
+    if (!grid || !params || !device_bytes || params->struct_size != sizeof(lbm_params)) return LBM_ERR_INVALID_ARG;
+    int D = 0, Q = 0;
+    if (lattice_dims(lattice, &D, &Q) != 0 || storage_bytes(params->storage) == 0) return LBM_ERR_INVALID_ARG;
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || (D == 2 && grid->nz != 1)) return LBM_ERR_INVALID_ARG;
+    const long long N = (long long)grid->nx * grid->ny * grid->nz;
+    if (N > (1LL << 31) - 1) return LBM_ERR_INVALID_ARG;
+    bool mask = !grid->periodic[0] || !grid->periodic[1] || (D == 3 && !grid->periodic[2]);
+    if (grid->solid)
+        for (long long i = 0; i < N && !mask; ++i) mask = grid->solid[i] != 0;
+    *device_bytes = footprint_bytes(Q, D, N, params->storage, params->inplace == 1, mask);
     return LBM_OK;
 }
 

@@ -1,0 +1,79 @@
+// Batched persistent launch of the split step over many lattices.
+//
+// A batch advances a set of independent lattices (same DdQq and storage,
+// any grid, parameters, walls and store layout each) with two launches per
+// time step for the whole set.  Work items are blocks of kSplitThreads
+// consecutive sites of one lattice; the grid is persistent (a fixed number
+// of blocks per SM, each looping over items), so one captured CUDA graph of
+// K steps stays valid while lattices join and leave: membership lives in a
+// device table that the host rewrites between graph launches.
+//
+// Table: BatchHeader, then members sorted by the number of steps they take
+// in the chunk (descending).  Launch k of the chunk (0 <= k < K) covers the
+// first active[k] items: exactly the members with take > k.
+#pragma once
+
+#include "lbm_split.cuh"
+
+namespace lbm {
+
+template <class R, class S>
+struct BatchMember {
+    SplitArgs<R, S> a[2];    // [k & 1]: arguments of the member's 1st, 2nd, ... step of the chunk
+    int mode[2];             // stream mode of those steps (ping-pong, AA odd/even)
+    long long first_item;    // prefix over members
+    long long items;
+    int take;                // steps in this chunk
+    int has_mask;
+};
+
+// Member owning item t (first_item ascending, t < total items).
+template <class R, class S>
+__device__ __forceinline__ int batch_find(const BatchMember<R, S> *__restrict__ mem, int nmem, long long t)
+{
+    int lo = 0, hi = nmem - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (mem[mid].first_item <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <class L, class R, class C, int PHASE, bool HAS_MASK, int MODE>
+__device__ __forceinline__ void batch_site(const SplitArgs<R, typename C::S> &a, int idx)
+{
+    // members have Q N < 2^32 (checked when they join): 32-bit indices
+    if constexpr (PHASE == 0) moments_site<L, R, C, HAS_MASK, MODE, uint32_t>(a, idx);
+    else collide_site<L, R, C, HAS_MASK, MODE, uint32_t>(a, idx);
+}
+
+// PHASE 0: S0 + S1 of every member; PHASE 1: S0 + S2..S5.
+template <class L, class R, class C, int PHASE>
+__global__ void __launch_bounds__(kSplitThreads, 3)
+    batch_kernel(const BatchHeader *__restrict__ hdr, const BatchMember<R, typename C::S> *__restrict__ mem, int k)
+{
+    using S = typename C::S;
+    const int nmem = (int)hdr->nmem;
+    const long long total = hdr->active[k];
+    for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+        const int j = batch_find(mem, nmem, t);
+        const int q = k & 1;
+        const SplitArgs<R, S> a = mem[j].a[q];
+        const int mode = mem[j].mode[q];
+        const long long lidx = (t - mem[j].first_item) * kSplitThreads + threadIdx.x;
+        if (lidx >= a.N) continue;
+        const int idx = (int)lidx;
+        if (mem[j].has_mask) {
+            if (mode == kPingPong) batch_site<L, R, C, PHASE, true, kPingPong>(a, idx);
+            else if (mode == kAAOdd) batch_site<L, R, C, PHASE, true, kAAOdd>(a, idx);
+            else batch_site<L, R, C, PHASE, true, kAAEven>(a, idx);
+        } else {
+            if (mode == kPingPong) batch_site<L, R, C, PHASE, false, kPingPong>(a, idx);
+            else if (mode == kAAOdd) batch_site<L, R, C, PHASE, false, kAAOdd>(a, idx);
+            else batch_site<L, R, C, PHASE, false, kAAEven>(a, idx);
+        }
+    }
+}
+
+}  // namespace lbm

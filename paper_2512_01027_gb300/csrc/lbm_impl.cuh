@@ -3,11 +3,13 @@
 #pragma once
 
 #include <algorithm>
+#include <cstring>
 
 #include "lbm_internal.h"
 #include "lbm_kernels.cuh"
 #include "lbm_step_v2.cuh"
 #include "lbm_split.cuh"
+#include "lbm_batch.cuh"
 
 #include <type_traits>
 
@@ -80,21 +82,29 @@ struct Impl {
         return cuda_fail(c, cudaGetLastError(), "step_kernel launch");
     }
 
-    template <int MODE>
-    static int launch_split(lbm_ctx *c, const SplitArgs<R, S> &a)
+    template <int MODE, class IX>
+    static void launch_split_ix(lbm_ctx *c, const SplitArgs<R, S> &a)
     {
         const unsigned blocks = (unsigned)((c->N + kSplitThreads - 1) / kSplitThreads);
         if (c->has_mask) {
-            moments_kernel<L, R, C, true, MODE><<<blocks, kSplitThreads, 0, c->stream>>>(a);
-            collide_kernel<L, R, C, true, MODE><<<blocks, kSplitThreads, 0, c->stream>>>(a);
+            moments_kernel<L, R, C, true, MODE, IX><<<blocks, kSplitThreads, 0, c->stream>>>(a);
+            collide_kernel<L, R, C, true, MODE, IX><<<blocks, kSplitThreads, 0, c->stream>>>(a);
         } else {
-            moments_kernel<L, R, C, false, MODE><<<blocks, kSplitThreads, 0, c->stream>>>(a);
-            collide_kernel<L, R, C, false, MODE><<<blocks, kSplitThreads, 0, c->stream>>>(a);
+            moments_kernel<L, R, C, false, MODE, IX><<<blocks, kSplitThreads, 0, c->stream>>>(a);
+            collide_kernel<L, R, C, false, MODE, IX><<<blocks, kSplitThreads, 0, c->stream>>>(a);
         }
+    }
+
+    template <int MODE>
+    static int launch_split(lbm_ctx *c, const SplitArgs<R, S> &a)
+    {
+        if (split_idx32(L::Q, c->N)) launch_split_ix<MODE, uint32_t>(c, a);
+        else launch_split_ix<MODE, long long>(c, a);
         return cuda_fail(c, cudaGetLastError(), "split step launch");
     }
 
-    static int step_split(lbm_ctx *c, int64_t n)
+    // Arguments of the split step taken with the ping-pong index cur ^ flip.
+    static SplitArgs<R, S> split_args(const lbm_ctx *c, int flip)
     {
         SplitArgs<R, S> a;
         a.mask = c->mask;
@@ -103,25 +113,83 @@ struct Impl {
         a.N = c->N;
         a.k = site_consts<R>(c->consts);
         a.phi = static_cast<R *>(c->phi);
+        const int src = c->cur ^ flip, dst = 1 - src;
+        a.src_h = static_cast<const S *>(c->h[src]);
+        a.src_g = static_cast<const S *>(c->g[src]);
+        a.dst_h = static_cast<S *>(c->h[dst]);
+        a.dst_g = static_cast<S *>(c->g[dst]);
+        a.P_old = static_cast<const R *>(c->P[src]);
+        a.P_new = static_cast<R *>(c->P[dst]);
+        a.u_old = static_cast<const R *>(c->u[src]);
+        a.u_new = static_cast<R *>(c->u[dst]);
+        return a;
+    }
+
+    // Stream mode of the step that follows `steps` completed steps.
+    static int split_mode(const lbm_ctx *c, int64_t steps)
+    {
+        if (!c->inplace) return kPingPong;
+        return steps % 2 == 0 ? kAAOdd : kAAEven;
+    }
+
+    static int step_split(lbm_ctx *c, int64_t n)
+    {
         for (int64_t s = 0; s < n; ++s) {
-            const int src = c->cur, dst = 1 - c->cur;
-            a.src_h = static_cast<const S *>(c->h[src]);
-            a.src_g = static_cast<const S *>(c->g[src]);
-            a.dst_h = static_cast<S *>(c->h[dst]);
-            a.dst_g = static_cast<S *>(c->g[dst]);
-            a.P_old = static_cast<const R *>(c->P[src]);
-            a.P_new = static_cast<R *>(c->P[dst]);
-            a.u_old = static_cast<const R *>(c->u[src]);
-            a.u_new = static_cast<R *>(c->u[dst]);
+            const SplitArgs<R, S> a = split_args(c, 0);
             int rc;
-            if (!c->inplace) rc = launch_split<kPingPong>(c, a);
-            else if (c->steps % 2 == 0) rc = launch_split<kAAOdd>(c, a);
+            const int mode = split_mode(c, c->steps);
+            if (mode == kPingPong) rc = launch_split<kPingPong>(c, a);
+            else if (mode == kAAOdd) rc = launch_split<kAAOdd>(c, a);
             else rc = launch_split<kAAEven>(c, a);
             if (rc != LBM_OK) return rc;
-            c->cur = dst;
+            c->cur = 1 - c->cur;
             c->steps += 1;
         }
         return LBM_OK;
+    }
+
+    // --- batched persistent launch (lbm_batch_*) ---------------------------
+    static size_t batch_member_bytes() { return sizeof(BatchMember<R, S>); }
+
+    static long long batch_items(const lbm_ctx *c) { return (c->N + kSplitThreads - 1) / kSplitThreads; }
+
+    static void batch_fill(const lbm_ctx *c, int take, long long first_item, void *dst)
+    {
+        BatchMember<R, S> m;
+        std::memset(&m, 0, sizeof m);
+        m.a[0] = split_args(c, 0);
+        m.a[1] = split_args(c, 1);
+        m.mode[0] = split_mode(c, c->steps);
+        m.mode[1] = split_mode(c, c->steps + 1);
+        m.first_item = first_item;
+        m.items = batch_items(c);
+        m.take = take;
+        m.has_mask = c->has_mask ? 1 : 0;
+        std::memcpy(dst, &m, sizeof m);
+    }
+
+    static int batch_grid(int phase)
+    {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (phase == 0)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<L, R, C, 0>, kSplitThreads, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<L, R, C, 1>, kSplitThreads, 0);
+        return (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    }
+
+    static cudaError_t batch_launch(cudaStream_t s, const void *d_table, int K, int grid0, int grid1)
+    {
+        const BatchHeader *hdr = static_cast<const BatchHeader *>(d_table);
+        const BatchMember<R, S> *mem = reinterpret_cast<const BatchMember<R, S> *>(
+            static_cast<const char *>(d_table) + batch_header_bytes());
+        for (int k = 0; k < K; ++k) {
+            batch_kernel<L, R, C, 0><<<grid0, kSplitThreads, 0, s>>>(hdr, mem, k);
+            batch_kernel<L, R, C, 1><<<grid1, kSplitThreads, 0, s>>>(hdr, mem, k);
+        }
+        return cudaGetLastError();
     }
 
     static int step(lbm_ctx *c, int64_t n)
@@ -244,7 +312,9 @@ struct Impl {
 
     static const Ops *ops()
     {
-        static const Ops o = {&init, &step, &read, &reduce, &pjump, &probe, &step_smem, &has_v2};
+        static const Ops o = {&init,      &step,       &read,         &reduce,      &pjump,
+                              &probe,     &step_smem,  &has_v2,       &batch_member_bytes,
+                              &batch_items, &batch_fill, &batch_grid, &batch_launch};
         return &o;
     }
 };

@@ -29,6 +29,17 @@ struct Allocator {
     void *ctx = nullptr;
 };
 
+// Head of a batch's device table (lbm_batch_*): the member count and, per
+// launch k of a chunk, the number of work items it covers.
+constexpr int kBatchMaxChunk = 64;
+
+struct BatchHeader {
+    long long nmem;
+    long long active[kBatchMaxChunk];
+};
+
+constexpr size_t batch_header_bytes() { return (sizeof(BatchHeader) + 255) / 256 * 256; }
+
 }  // namespace lbm
 
 struct lbm_ctx {
@@ -62,6 +73,27 @@ struct lbm_ctx {
     const lbm::Ops *ops = nullptr;
     lbm::Allocator allocator;
     std::vector<void *> owned;
+    lbm_batch_ctx *batch = nullptr;   // the batch this handle belongs to, if any
+};
+
+// A set of handles stepped together by the batched kernels.
+struct lbm_batch_ctx {
+    int lattice = 0, storage = 0, device = 0;
+    const lbm::Ops *ops = nullptr;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<lbm_ctx *> members;
+    std::vector<int64_t> remaining;   // steps each member still has to take
+    int chunk = 16;                   // steps per chunk (one graph launch)
+    bool use_graph = true;
+    size_t table_bytes = 0;           // header + capacity members
+    size_t cap_members = 0;
+    void *d_table = nullptr;
+    void *h_table = nullptr;          // pinned staging copy
+    std::vector<std::pair<int, cudaGraphExec_t>> graphs;   // per chunk length
+    int grid[2] = {0, 0};
+    int64_t launches = 0;             // kernels launched so far
+    std::string err;
 };
 
 namespace lbm {
@@ -76,12 +108,39 @@ struct Ops {
     int (*probe)(lbm_ctx *c, const long long *d_sites, int n, double *d_h, double *d_g, double *d_P, double *d_u);
     size_t (*step_smem)();
     bool (*has_v2)();
+    // batched persistent launch (lbm_batch_*)
+    size_t (*batch_member_bytes)();
+    long long (*batch_items)(const lbm_ctx *c);
+    void (*batch_fill)(const lbm_ctx *c, int take, long long first_item, void *dst);
+    int (*batch_grid)(int phase);
+    cudaError_t (*batch_launch)(cudaStream_t s, const void *d_table, int K, int grid0, int grid1);
 };
 
-const Ops *ops_f64(int lattice);
-const Ops *ops_f32(int lattice);
-const Ops *ops_f16(int lattice);
-const Ops *ops_bf16(int lattice);
+// One instantiation per (storage, lattice); lattice 0 D2Q9, 1 D3Q19, 2 D3Q27.
+const Ops *ops_f64_lat0();
+const Ops *ops_f64_lat1();
+const Ops *ops_f64_lat2();
+const Ops *ops_f32_lat0();
+const Ops *ops_f32_lat1();
+const Ops *ops_f32_lat2();
+const Ops *ops_f16_lat0();
+const Ops *ops_f16_lat1();
+const Ops *ops_f16_lat2();
+const Ops *ops_bf16_lat0();
+const Ops *ops_bf16_lat1();
+const Ops *ops_bf16_lat2();
+
+inline const Ops *ops_for(int lattice, int storage)
+{
+    static const Ops *(*const table[4][3])() = {
+        {ops_f64_lat0, ops_f64_lat1, ops_f64_lat2},
+        {ops_f32_lat0, ops_f32_lat1, ops_f32_lat2},
+        {ops_f16_lat0, ops_f16_lat1, ops_f16_lat2},
+        {ops_bf16_lat0, ops_bf16_lat1, ops_bf16_lat2},
+    };
+    if (storage < 0 || storage > 3 || lattice < 0 || lattice > 2) return nullptr;
+    return table[storage][lattice]();
+}
 
 // Device memory through the handle's allocator.
 void *dev_alloc(lbm_ctx *c, size_t bytes);

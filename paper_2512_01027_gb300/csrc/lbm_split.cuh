@@ -30,68 +30,106 @@
 
 namespace lbm {
 
-// Offset (slot * N + site) from which f_i(x) is read, for the stream mode.
-template <class L, int MODE, int i>
-__device__ __forceinline__ long long read_off(const Nbr &nb, long long idx, long long N, uint32_t m, bool has_mask)
+// Site coordinates and wrapped neighbour offsets in 32 bits (N < 2^31 sites):
+// the site x + s c is xo[1 + s c_x] + yo[1 + s c_y] + zo[1 + s c_z].  Slot i
+// of a population set is its own plane base + (size_t)i * N, a value uniform
+// across the grid, so an access costs one 32-bit offset and one wide
+// multiply-add on top of the load.
+struct Nbr32 {
+    int xo[3], yo[3], zo[3];
+    __device__ __forceinline__ Nbr32(int idx, int nx, int ny, int nz)
+    {
+        const int x = idx % nx;
+        const int y = (idx / nx) % ny;
+        const int z = idx / (nx * ny);
+        const int nxy = nx * ny;
+        xo[0] = wrapc(x - 1, nx); xo[1] = x; xo[2] = wrapc(x + 1, nx);
+        yo[0] = wrapc(y - 1, ny) * nx; yo[1] = y * nx; yo[2] = wrapc(y + 1, ny) * nx;
+        zo[0] = wrapc(z - 1, nz) * nxy; zo[1] = z * nxy; zo[2] = wrapc(z + 1, nz) * nxy;
+    }
+    template <class L, int i>
+    __device__ __forceinline__ int at(int s) const
+    {
+        constexpr int cx = L::c(i, 0), cy = L::c(i, 1), cz = L::c(i, 2);
+        if (s > 0) return xo[1 + cx] + yo[1 + cy] + zo[1 + cz];
+        return xo[1 - cx] + yo[1 - cy] + zo[1 - cz];
+    }
+};
+
+// Element index slot * N + off in the index type IX: 32-bit unsigned when
+// Q N < 2^32 (one multiply-add per access, no 64-bit arithmetic), else
+// 64-bit.
+template <class IX>
+__device__ __forceinline__ IX eidx(int slot, IX N, int off)
+{
+    return (IX)slot * N + (IX)off;
+}
+
+// Index at which f_i(x) is read, for the stream mode.
+template <class L, int MODE, int i, class IX>
+__device__ __forceinline__ IX read_idx(IX N, const Nbr32 &nb, int idx, uint32_t m, bool has_mask)
 {
     if constexpr (i == 0) {
-        return idx;                                   // rest population never moves
+        return (IX)idx;                               // rest population never moves
     } else {
         const bool bb = has_mask && ((m >> i) & 1u);  // x - c_i solid/outside
-        if constexpr (MODE == kPingPong) return bb ? (long long)opp(i) * N + idx : (long long)i * N + nb.at<L, i>(-1);
-        else if constexpr (MODE == kAAEven) return (long long)i * N + idx;
-        else return bb ? (long long)i * N + idx : (long long)opp(i) * N + nb.at<L, i>(-1);
+        if constexpr (MODE == kPingPong)
+            return bb ? eidx<IX>(opp(i), N, idx) : eidx<IX>(i, N, nb.at<L, i>(-1));
+        else if constexpr (MODE == kAAEven)
+            return eidx<IX>(i, N, idx);
+        else
+            return bb ? eidx<IX>(i, N, idx) : eidx<IX>(opp(i), N, nb.at<L, i>(-1));
     }
 }
 
-// Offset to which f*_i(x) is written, for the stream mode.
-template <class L, int MODE, int i>
-__device__ __forceinline__ long long write_off(const Nbr &nb, long long idx, long long N, uint32_t m, bool has_mask)
+// Index to which f*_i(x) is written, for the stream mode.
+template <class L, int MODE, int i, class IX>
+__device__ __forceinline__ IX write_idx(IX N, const Nbr32 &nb, int idx, uint32_t m, bool has_mask)
 {
     if constexpr (i == 0) {
-        return idx;
+        return (IX)idx;
     } else if constexpr (MODE == kPingPong) {
-        return (long long)i * N + idx;
+        return eidx<IX>(i, N, idx);
     } else if constexpr (MODE == kAAEven) {
-        return (long long)opp(i) * N + idx;
+        return eidx<IX>(opp(i), N, idx);
     } else {
         const bool bb = has_mask && ((m >> opp(i)) & 1u);   // x + c_i solid/outside
-        return bb ? (long long)opp(i) * N + idx : (long long)i * N + nb.at<L, i>(1);
+        return bb ? eidx<IX>(opp(i), N, idx) : eidx<IX>(i, N, nb.at<L, i>(1));
     }
 }
 
 constexpr int kSplitThreads = 128;
+constexpr int kSplitMinBlocks = 4;   // <= 128 registers a thread: 16 warps an SM
 
-template <class L, class R, class C, bool HAS_MASK, int MODE>
-__global__ void __launch_bounds__(kSplitThreads) moments_kernel(const SplitArgs<R, typename C::S> a)
+// S0 + S1 at site idx (0 <= idx < a.N).
+template <class L, class R, class C, bool HAS_MASK, int MODE, class IX>
+__device__ __forceinline__ void moments_site(const SplitArgs<R, typename C::S> &a, const int idx)
 {
     constexpr int D = L::D, Q = L::Q;
-    const long long idx = (long long)blockIdx.x * kSplitThreads + threadIdx.x;
-    if (idx >= a.N) return;
     uint32_t m = 0;
     if constexpr (HAS_MASK) m = a.mask[idx];
     if (m & kSolidBit) return;
-    const long long N = a.N;
-    const Nbr nb(idx, a.nx, a.ny, D == 3 ? a.nz : 1);
+    const IX N = (IX)a.N;
+    const Nbr32 nb(idx, a.nx, a.ny, D == 3 ? a.nz : 1);
     R hp[Q], gp[Q], Pn[Q], K[Q];
     const R P0 = a.P_old[idx];
     R sum_wcu = R(0);
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        const long long off = read_off<L, MODE, i>(nb, idx, N, m, HAS_MASK);
-        hp[i] = C::template dec_h<i>(a.src_h[off]);
-        gp[i] = C::template dec_g<i>(a.src_g[off]);
+        const IX e = read_idx<L, MODE, i, IX>(N, nb, idx, m, HAS_MASK);
+        hp[i] = C::template dec_h<i>(a.src_h[e]);
+        gp[i] = C::template dec_g<i>(a.src_g[e]);
         if constexpr (i == 0) {
             Pn[0] = P0;
         } else {
             const bool bb = HAS_MASK && ((m >> i) & 1u);
-            const long long src = nb.at<L, i>(-1);
+            const int src = nb.at<L, i>(-1);
             Pn[i] = bb ? P0 : a.P_old[src];
             if (!bb) {
                 R un[3];
                 static_for<0, 3>([&](auto A) {
                     constexpr int ax = decltype(A)::value;
-                    if constexpr (ax < D && L::c(i, ax) != 0) un[ax] = a.u_old[(long long)ax * N + src];
+                    if constexpr (ax < D && L::c(i, ax) != 0) un[ax] = a.u_old[eidx<IX>(ax, N, src)];
                     else un[ax] = R(0);
                 });
                 sum_wcu = sum_wcu + R(L::w(i)) * dot_c<L, i>(un);
@@ -111,21 +149,20 @@ __global__ void __launch_bounds__(kSplitThreads) moments_kernel(const SplitArgs<
     a.P_new[idx] = Pnew;
     static_for<0, D>([&](auto A) {
         constexpr int ax = decltype(A)::value;
-        a.u_new[(long long)ax * N + idx] = u[ax];
+        a.u_new[eidx<IX>(ax, N, idx)] = u[ax];
     });
 }
 
-template <class L, class R, class C, bool HAS_MASK, int MODE>
-__global__ void __launch_bounds__(kSplitThreads) collide_kernel(const SplitArgs<R, typename C::S> a)
+// S0 + S2..S5 at site idx (0 <= idx < a.N).
+template <class L, class R, class C, bool HAS_MASK, int MODE, class IX>
+__device__ __forceinline__ void collide_site(const SplitArgs<R, typename C::S> &a, const int idx)
 {
     constexpr int D = L::D, Q = L::Q;
-    const long long idx = (long long)blockIdx.x * kSplitThreads + threadIdx.x;
-    if (idx >= a.N) return;
     uint32_t m = 0;
     if constexpr (HAS_MASK) m = a.mask[idx];
     if (m & kSolidBit) return;
-    const long long N = a.N;
-    const Nbr nb(idx, a.nx, a.ny, D == 3 ? a.nz : 1);
+    const IX N = (IX)a.N;
+    const Nbr32 nb(idx, a.nx, a.ny, D == 3 ? a.nz : 1);
     // S2: stencils of phi^{n+1} and u^{n+1} from the fields of the moments launch
     const R phi = a.phi[idx];
     R gphi[3], lphi;
@@ -136,11 +173,10 @@ __global__ void __launch_bounds__(kSplitThreads) collide_kernel(const SplitArgs<
     gu[0][2] = gu[1][2] = gu[2][0] = gu[2][1] = gu[2][2] = R(0);
     static_for<0, D>([&](auto A) {
         constexpr int ax = decltype(A)::value;
-        const R *f = a.u_new + (long long)ax * N;
-        u[ax] = f[idx];
+        u[ax] = a.u_new[eidx<IX>(ax, N, idx)];
         R lap_unused;
-        stencil_any<L, R>([&](auto I, int s) { return f[nb.at<L, decltype(I)::value>(s)]; }, m, u[ax], R(0),
-                          gu[ax], lap_unused);
+        stencil_any<L, R>([&](auto I, int s) { return a.u_new[eidx<IX>(ax, N, nb.at<L, decltype(I)::value>(s))]; },
+                          m, u[ax], R(0), gu[ax], lap_unused);
     });
     const R phihat = a.k.clamp ? clamp01(phi) : phi;
     const R rho = a.k.rho_a + phihat * a.k.drho;
@@ -148,19 +184,37 @@ __global__ void __launch_bounds__(kSplitThreads) collide_kernel(const SplitArgs<
     R hp[Q], gp[Q], hs[Q], gs[Q];
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        const long long off = read_off<L, MODE, i>(nb, idx, N, m, HAS_MASK);
-        hp[i] = C::template dec_h<i>(a.src_h[off]);
-        gp[i] = C::template dec_g<i>(a.src_g[off]);
+        const IX e = read_idx<L, MODE, i, IX>(N, nb, idx, m, HAS_MASK);
+        hp[i] = C::template dec_h<i>(a.src_h[e]);
+        gp[i] = C::template dec_g<i>(a.src_g[e]);
     });
     collide<L, R, false, C::kPdev>(a.k, phi, phihat, rho, P, u, gphi, lphi, gu, hp, gp, hs, gs);
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        const long long off = write_off<L, MODE, i>(nb, idx, N, m, HAS_MASK);
-        a.dst_h[off] = C::template enc_h<i>(hs[i]);
-        a.dst_g[off] = C::template enc_g<i>(gs[i]);
+        const IX e = write_idx<L, MODE, i, IX>(N, nb, idx, m, HAS_MASK);
+        a.dst_h[e] = C::template enc_h<i>(hs[i]);
+        a.dst_g[e] = C::template enc_g<i>(gs[i]);
     });
     if (!(isfinite(phi) && isfinite(P) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2])))
         atomicOr(a.err, 1);
 }
+
+template <class L, class R, class C, bool HAS_MASK, int MODE, class IX>
+__global__ void __launch_bounds__(kSplitThreads, kSplitMinBlocks) moments_kernel(const SplitArgs<R, typename C::S> a)
+{
+    const long long idx = (long long)blockIdx.x * kSplitThreads + threadIdx.x;
+    if (idx < a.N) moments_site<L, R, C, HAS_MASK, MODE, IX>(a, (int)idx);
+}
+
+template <class L, class R, class C, bool HAS_MASK, int MODE, class IX>
+__global__ void __launch_bounds__(kSplitThreads, kSplitMinBlocks) collide_kernel(const SplitArgs<R, typename C::S> a)
+{
+    const long long idx = (long long)blockIdx.x * kSplitThreads + threadIdx.x;
+    if (idx < a.N) collide_site<L, R, C, HAS_MASK, MODE, IX>(a, (int)idx);
+}
+
+// True when every element index of the lattice's population sets fits in 32
+// bits, so the kernels can take the 32-bit index path.
+inline bool split_idx32(int Q, long long N) { return (unsigned long long)Q * (unsigned long long)N < (1ULL << 32); }
 
 }  // namespace lbm

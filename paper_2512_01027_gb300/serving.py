@@ -1,0 +1,190 @@
+"""Serving loop: many independent multiphase LB solves on one GPU.
+
+A request names one simulation (grid edge, droplet radius, density ratio,
+surface tension, number of steps).  The server
+
+* takes requests as they arrive (arrival times in seconds from the start),
+* builds each request's initial fields on host threads while the GPU works,
+* admits requests first-come first-served while their device footprint
+  (``estimate_footprint``) fits in the HBM budget and a member slot is free,
+* advances all admitted lattices together through one ``Batch`` (two kernel
+  launches per time step for the whole set, chunks replayed as CUDA graphs),
+  each lattice by exactly its own number of steps,
+* retires a lattice the moment its steps are done: reads its fields back to
+  the host, frees its memory, and admits the next request in its place
+  (continuous batching).
+
+Latency is arrival -> result on the host.  The per-site arithmetic of a
+batch does not depend on the other members, so a request's result is the
+same whether it is served alone or in any mix.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from concurrent.futures import ThreadPoolExecutor
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import Batch, Lattice, estimate_footprint
+
+
+@dataclass
+class Served:
+    rid: int
+    arrival: float
+    admitted: float
+    finished: float
+    steps: int
+    sites: int
+    fields: tuple | None = None
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+@dataclass
+class ServeStats:
+    results: list = field(default_factory=list)
+    makespan: float = 0.0
+    peak_members: int = 0
+    peak_bytes: int = 0
+    launches: int = 0
+
+    def summary(self) -> dict:
+        lat = np.array([r.latency for r in self.results]) if self.results else np.zeros(1)
+        sites = sum(r.sites * r.steps for r in self.results)
+        return {
+            "requests": len(self.results),
+            "solves_per_s": len(self.results) / self.makespan if self.makespan > 0 else 0.0,
+            "mlups": sites / self.makespan / 1e6 if self.makespan > 0 else 0.0,
+            "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)),
+            "makespan_s": self.makespan,
+            "peak_members": self.peak_members,
+            "peak_gb": self.peak_bytes / 1e9,
+            "gpu_launches": self.launches,
+        }
+
+
+def _prepare(req):
+    c = req.case()
+    return c
+
+
+class Server:
+    """Continuous-batching server for requests of one lattice and storage."""
+
+    def __init__(self, lattice: str = "D3Q27", storage: str = "f16", inplace: bool = True, chunk: int = 16,
+                 max_members: int = 64, hbm_budget: int | None = None, prep_threads: int = 4,
+                 keep_fields: bool = False, stream=None):
+        self.lattice, self.storage, self.inplace = lattice, storage, bool(inplace)
+        self.chunk, self.max_members = int(chunk), int(max_members)
+        self.keep_fields = keep_fields
+        if hbm_budget is None:
+            import torch
+
+            free, _total = torch.cuda.mem_get_info()
+            hbm_budget = int(0.85 * free)
+        self.hbm_budget = int(hbm_budget)
+        self.prep_threads = prep_threads
+        self.batch = Batch(lattice, storage)
+        self.batch.set_tuning(chunk=self.chunk, use_graph=True)
+        if stream is not None:
+            self.batch.set_stream(stream)
+
+    def footprint(self, req) -> int:
+        n = req.edge
+        return estimate_footprint(self.lattice, (n, n, n), storage=self.storage, inplace=int(self.inplace))
+
+    def close(self):
+        self.batch.close()
+
+    def run(self, requests, clock=time.perf_counter) -> ServeStats:
+        pend = collections.deque(sorted(requests, key=lambda r: r.arrival))
+        waiting = collections.deque()          # (request, future of its initial fields)
+        active = []                            # (request, Lattice, bytes, admitted)
+        stats = ServeStats()
+        used = 0
+        launches0 = self.batch.info()[1]
+        with ThreadPoolExecutor(max_workers=self.prep_threads) as pool:
+            t0 = clock()
+            while pend or waiting or active:
+                now = clock() - t0
+                while pend and pend[0].arrival <= now:
+                    r = pend.popleft()
+                    waiting.append((r, pool.submit(_prepare, r)))
+                # admission: first come first served, by free HBM and slots
+                while waiting and len(active) < self.max_members:
+                    r, fut = waiting[0]
+                    need = self.footprint(r)
+                    if need > self.hbm_budget:
+                        raise ValueError(f"request {r.rid} needs {need} bytes, more than the HBM budget")
+                    if used + need > self.hbm_budget:
+                        break
+                    if active and not fut.done():
+                        break                  # keep the GPU busy; admit it next round
+                    c = fut.result()
+                    waiting.popleft()
+                    prm = {k: v for k, v in c.params.items() if k != "g_ext"}
+                    L = Lattice(c.lattice, c.shape, periodic=c.periodic, solid=c.solid, storage=self.storage,
+                                g_ext=c.params.get("g_ext", (0, 0, 0)), inplace=int(self.inplace), **prm)
+                    L.init_fields(c.phi0, c.P0, c.u0)
+                    self.batch.add(L, r.steps)
+                    used += need
+                    active.append((r, L, need, clock() - t0))
+                stats.peak_members = max(stats.peak_members, len(active))
+                stats.peak_bytes = max(stats.peak_bytes, used)
+                if not active:
+                    if waiting:
+                        waiting[0][1].result()
+                    elif pend:
+                        time.sleep(max(0.0, min(pend[0].arrival - (clock() - t0), 0.002)))
+                    continue
+                self.batch.step(self.chunk)
+                keep = []
+                for r, L, need, t_adm in active:
+                    if self.batch.remaining(L) == 0:
+                        out = L.read_fields()
+                        t_fin = clock() - t0
+                        self.batch.remove(L)
+                        L.close()
+                        used -= need
+                        stats.results.append(Served(r.rid, r.arrival, t_adm, t_fin, r.steps, L.N,
+                                                    out if self.keep_fields else None))
+                    else:
+                        keep.append((r, L, need, t_adm))
+                active = keep
+            stats.makespan = clock() - t0
+        stats.launches = self.batch.info()[1] - launches0
+        stats.results.sort(key=lambda s: s.rid)
+        return stats
+
+
+def run_one_at_a_time(requests, storage: str = "f32", clock=time.perf_counter) -> ServeStats:
+    """The same trace served without batching: one lattice at a time, in
+    arrival order, each stepped with its own launches (split form)."""
+    stats = ServeStats()
+    t0 = clock()
+    launches = 0
+    for r in sorted(requests, key=lambda q: q.arrival):
+        while clock() - t0 < r.arrival:
+            time.sleep(min(0.002, r.arrival - (clock() - t0)))
+        c = r.case()
+        t_adm = clock() - t0
+        prm = {k: v for k, v in c.params.items() if k != "g_ext"}
+        L = Lattice(c.lattice, c.shape, periodic=c.periodic, solid=c.solid, storage=storage,
+                    g_ext=c.params.get("g_ext", (0, 0, 0)), **prm)
+        L.init_fields(c.phi0, c.P0, c.u0)
+        L.step(r.steps)
+        L.read_fields()
+        launches += 2 * r.steps
+        t_fin = clock() - t0
+        stats.results.append(Served(r.rid, r.arrival, t_adm, t_fin, r.steps, L.N))
+        L.close()
+    stats.makespan = clock() - t0
+    stats.peak_members = 1
+    stats.launches = launches
+    return stats

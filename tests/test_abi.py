@@ -104,3 +104,31 @@ def test_no_cpu_fallback_without_a_device():
     rc, h = _create()
     assert rc == lbm.LBM_ERR_CUDA
     assert b"CUDA" in lbm.lib().lbm_last_error(None) or b"device" in lbm.lib().lbm_last_error(None)
+
+
+def test_footprint_estimate_needs_no_device():
+    """Admission control sizes a lattice before creating it: populations
+    (2 sets in place, 4 ping-pong), P, u (two each), phi, scratch, mask."""
+    N = 32 ** 3
+    scratch = 8 * (1024 * 8 + 64) + 256
+    got = lbm.estimate_footprint("D3Q27", (32, 32, 32), storage="f16", inplace=1)
+    assert got == 2 * 27 * N * 2 + 9 * N * 4 + scratch
+    got = lbm.estimate_footprint("D3Q27", (32, 32, 32), periodic=(1, 1, 0), storage="f32")
+    assert got == 4 * 27 * N * 4 + 9 * N * 4 + scratch + 4 * N
+    got = lbm.estimate_footprint("D2Q9", (16, 8, 1), storage="f64")
+    assert got == 4 * 9 * 128 * 8 + 7 * 128 * 8 + scratch
+    solid = np.zeros((1, 8, 16), np.uint8)
+    solid[0, 3, 3] = 1
+    assert lbm.estimate_footprint("D2Q9", (16, 8, 1), solid=solid, storage="f64") == got + 4 * 128
+    with pytest.raises(lbm.LbmError):
+        lbm.estimate_footprint("D2Q9", (16, 8, 2))
+
+
+def test_batch_calls_without_a_batch_fail_cleanly():
+    L = lbm.lib()
+    assert L.lbm_batch_step(None, 1, None) == lbm.LBM_ERR_INVALID_ARG
+    assert L.lbm_batch_destroy(None) == lbm.LBM_ERR_INVALID_ARG
+    assert L.lbm_batch_add(None, None, 1) == lbm.LBM_ERR_INVALID_ARG
+    assert L.lbm_autotune(None, 1, None, None, None) == lbm.LBM_ERR_INVALID_ARG
+    out = ctypes.c_void_p()
+    assert L.lbm_batch_create(7, 1, ctypes.byref(out)) == lbm.LBM_ERR_INVALID_ARG

@@ -1,0 +1,157 @@
+"""Batched persistent launch (lbm_batch_*) and the autotuner.
+
+A batch steps many lattices with two launches per time step for the whole
+set.  Each site's arithmetic is the split form's, in one kernel whatever the
+membership, so a lattice's results must not depend on its batch-mates
+(bitwise), FP64 members must reproduce the oracle bit for bit, and step
+budgets, chunking and graph replay must not change anything either.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from test_gpu_parity import closed_box_3d, run_oracle, small_3d
+
+pytestmark = pytest.mark.gpu
+
+
+def make(lbm, c, storage="f64", inplace=0):
+    prm = {k: v for k, v in c.params.items() if k != "g_ext"}
+    L = lbm.Lattice(c.lattice, c.shape, periodic=c.periodic, solid=c.solid, storage=storage,
+                    g_ext=c.params.get("g_ext", (0, 0, 0)), inplace=inplace, **prm)
+    L.init_fields(c.phi0, c.P0, c.u0)
+    return L
+
+
+def cases_d3q19():
+    a = small_3d("D3Q19")                                   # walls, ragged tiles
+    b = closed_box_3d("D3Q19")                              # random solids, closed
+    c = small_3d("D3Q19", nx=9, ny=7, nz=5, walls=False)    # periodic, thin
+    return [a, b, c]
+
+
+def test_batch_f64_matches_oracle(lbm):
+    """Three different lattices (grids, walls, layouts) in one batch, budgets
+    37 / 50 / 23 steps over chunks of 16: each equals the oracle bit for bit."""
+    cs = cases_d3q19()
+    budgets = [37, 50, 23]
+    B = lbm.Batch("D3Q19", "f64")
+    Ls = [make(lbm, c, "f64", inplace=j % 2) for j, c in enumerate(cs)]
+    for L, n in zip(Ls, budgets):
+        B.add(L, n)
+    assert B.step(100) == 3
+    for L, c, n in zip(Ls, cs, budgets):
+        assert L.steps_done == n
+        assert B.remaining(L) == 0
+        g = L.read_fields()
+        _, o = run_oracle(c, n)
+        for x, y in zip(g, o):
+            assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_alone_vs_mixed_bitwise(lbm, storage):
+    """A lattice stepped alone in a batch and stepped among others (which
+    join late, leave early and use the other store layout) ends bit for bit
+    the same; so do graph replay and plain launches, and any chunk length."""
+    c = W.droplet_3d(24)
+    others = [small_3d("D3Q27"), closed_box_3d("D3Q27"), small_3d("D3Q27", nx=40, ny=12, nz=21)]
+    n = 41
+
+    B1 = lbm.Batch("D3Q27", storage)
+    A1 = make(lbm, c, storage)
+    B1.add(A1, n)
+    B1.step(n)
+    want = A1.read_fields()
+
+    B2 = lbm.Batch("D3Q27", storage)
+    B2.set_tuning(chunk=5, use_graph=True)
+    A2 = make(lbm, c, storage)
+    O = [make(lbm, oc, storage, inplace=j % 2) for j, oc in enumerate(others)]
+    B2.add(A2, n)
+    B2.add(O[0], 7)                   # finishes inside the first chunks
+    B2.step(12)
+    B2.add(O[1], 100)                 # joins late
+    B2.add(O[2], 100)
+    B2.step(10)
+    B2.remove(O[1])                   # leaves early
+    B2.step(100)
+    assert A2.steps_done == n and O[0].steps_done == 7
+    for x, y in zip(want, A2.read_fields()):
+        assert np.array_equal(x, y)
+
+    B3 = lbm.Batch("D3Q27", storage)
+    B3.set_tuning(chunk=1, use_graph=False)
+    A3 = make(lbm, c, storage)
+    B3.add(A3, n)
+    B3.step(n)
+    for x, y in zip(want, A3.read_fields()):
+        assert np.array_equal(x, y)
+
+
+def test_batch_matches_single_lattice_split(lbm):
+    """The batch kernels and the single-lattice split kernels evaluate the
+    same per-site code: FP64 bit for bit, FP32 to rounding."""
+    c = small_3d("D3Q27")
+    for storage in ("f64", "f32"):
+        S = make(lbm, c, storage)
+        S.set_tuning(3, 0)
+        S.step(30)
+        B = lbm.Batch("D3Q27", storage)
+        L = make(lbm, c, storage)
+        B.add(L, 30)
+        B.step(30)
+        for x, y in zip(S.read_fields(), L.read_fields()):
+            if storage == "f64":
+                assert np.array_equal(x, y)
+            else:
+                assert np.abs(x - y).max() <= 1e-5 * max(np.abs(x).max(), 1e-30)
+
+
+def test_batch_rules(lbm):
+    c = small_3d("D3Q27")
+    B = lbm.Batch("D3Q27", "f32")
+    L = make(lbm, c, "f32")
+    B.add(L, 10)
+    with pytest.raises(lbm.LbmError) as e:
+        L.step(1)                      # stepped by its batch only
+    assert e.value.code == lbm.LBM_ERR_INVALID_ARG
+    with pytest.raises(lbm.LbmError):
+        B.add(L, 5)                    # already a member
+    with pytest.raises(lbm.LbmError):
+        B.add(make(lbm, c, "f16"), 5)  # other storage
+    with pytest.raises(lbm.LbmError):
+        B.set_tuning(chunk=65)
+    assert B.step(4) == 0 and B.remaining(L) == 6
+    m, launches = B.info()
+    assert m == 1 and launches == 2 * 4
+    L.read_fields()                    # readable between batch steps
+    B.remove(L)
+    L.step(2)                          # its own again
+    assert L.steps_done == 6
+    # destroying a member detaches it
+    L2 = make(lbm, c, "f32")
+    B.add(L2, 3)
+    L2.close()
+    B.members.remove(L2)
+    assert B.info()[0] == 0
+    assert B.step(5) == 0
+
+
+def test_autotune_keeps_state(lbm):
+    c = small_3d("D3Q27", nx=48, ny=24, nz=20)
+    L = make(lbm, c, "f32")
+    L.step(3)
+    v, z, ms = L.autotune(3)
+    assert v in (1, 2, 3) and ms > 0
+    assert L.steps_done == 3
+    L.step(5)
+    R = make(lbm, c, "f32")
+    R.step(3)
+    R.set_tuning(v, z)
+    R.step(5)
+    for x, y in zip(R.read_fields(), L.read_fields()):
+        assert np.array_equal(x, y)
+    # an in-place store has one form
+    I = make(lbm, c, "f32", inplace=1)
+    assert I.autotune(2)[0] == 3
