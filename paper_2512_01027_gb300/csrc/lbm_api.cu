@@ -134,6 +134,7 @@ size_t footprint_bytes(int Q, int D, long long N, int storage, bool inplace, boo
     const size_t pop = (size_t)Q * (size_t)N * storage_bytes(storage);
     const size_t field = (size_t)N * compute_bytes(storage);
     size_t s = (inplace ? 2 : 4) * pop + (3 + 2 * (size_t)D) * field + sizeof(double) * kScratchDoubles + 256;
+    if (storage != LBM_STORE_F64) s += 2 * sizeof(float) * 4 * (size_t)N;   // packed (u, P), ping-pong
     if (has_mask) s += sizeof(uint32_t) * (size_t)N;
     return s;
 }
@@ -322,8 +323,13 @@ int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params, lbm_
         }
     }
     c->phi = own(c, c->field_bytes);
+    if (storage != LBM_STORE_F64)
+        for (int b = 0; b < 2 && c->phi; ++b) {
+            c->f4[b] = own(c, sizeof(float) * 4 * (size_t)N);
+            if (!c->f4[b]) c->phi = nullptr;
+        }
     if (!c->phi) {
-        g_create_err = "device allocation of the phi field failed";
+        g_create_err = "device allocation of the phi or packed (u, P) fields failed";
         release(c);
         delete c;
         return LBM_ERR_OOM;
@@ -600,6 +606,7 @@ int lbm_load_state(lbm_handle h, const void *host_buf, size_t bytes)
     if (rc == LBM_OK) rc = cuda_fail(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream), "cudaMemsetAsync(err)");
     if (rc == LBM_OK) rc = cuda_fail(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     if (rc == LBM_OK) std::memcpy(&h->steps, p, sizeof(int64_t));
+    h->f4_valid = false;
     return rc;
 }
 

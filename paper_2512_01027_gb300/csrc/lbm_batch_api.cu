@@ -211,6 +211,17 @@ int lbm_batch_step(lbm_batch b, int64_t n, int *finished)
             if (take[j] > 0) order.push_back((int)j);
         }
         if (order.empty()) break;
+        // packed (u, P) words of members whose state was (re)loaded or fused-stepped
+        for (int j : order) {
+            lbm_ctx *h = b->members[j];
+            if (h->f4_valid) continue;
+            rc = b->ops->pack(h);
+            if (rc == LBM_OK) rc = bcuda(b, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize(member)");
+            if (rc != LBM_OK) {
+                b->err = "packing a member's state failed: " + h->err;
+                return rc;
+            }
+        }
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return take[x] > take[y]; });
         // table: header + members by descending take
         BatchHeader hdr;

@@ -114,6 +114,8 @@ struct Impl {
         a.k = site_consts<R>(c->consts);
         a.phi = static_cast<R *>(c->phi);
         const int src = c->cur ^ flip, dst = 1 - src;
+        a.F_old = static_cast<const float4 *>(c->f4[src]);
+        a.F_new = static_cast<float4 *>(c->f4[dst]);
         a.src_h = static_cast<const S *>(c->h[src]);
         a.src_g = static_cast<const S *>(c->g[src]);
         a.dst_h = static_cast<S *>(c->h[dst]);
@@ -132,8 +134,29 @@ struct Impl {
         return steps % 2 == 0 ? kAAOdd : kAAEven;
     }
 
+    // Packed (u, P) words of the current state, when they are stale.
+    static int pack(lbm_ctx *c)
+    {
+        if constexpr (kPacked<R>) {
+            if (c->f4_valid || !c->f4[c->cur]) return LBM_OK;
+            const unsigned blocks = (unsigned)((c->N + 255) / 256);
+            pack_kernel<L::D><<<blocks, 256, 0, c->stream>>>(static_cast<const float *>(c->P[c->cur]),
+                                                             static_cast<const float *>(c->u[c->cur]),
+                                                             static_cast<float4 *>(c->f4[c->cur]), c->N);
+            const int rc = cuda_fail(c, cudaGetLastError(), "pack_kernel launch");
+            if (rc == LBM_OK) c->f4_valid = true;
+            return rc;
+        } else {
+            return LBM_OK;
+        }
+    }
+
     static int step_split(lbm_ctx *c, int64_t n)
     {
+        if (n > 0) {
+            const int rc = pack(c);
+            if (rc != LBM_OK) return rc;
+        }
         for (int64_t s = 0; s < n; ++s) {
             const SplitArgs<R, S> a = split_args(c, 0);
             int rc;
@@ -219,6 +242,7 @@ struct Impl {
             if (rc != LBM_OK) return rc;
             c->cur = dst;
             c->steps += 1;
+            c->f4_valid = false;   // the fused kernels do not write the packed words
         }
         return LBM_OK;
     }
@@ -242,6 +266,7 @@ struct Impl {
         else init_kernel<L, R, C, false><<<blocks, threads, 0, c->stream>>>(a);
         c->cur = 0;
         c->steps = 0;
+        c->f4_valid = false;
         return cuda_fail(c, cudaGetLastError(), "init_kernel launch");
     }
 
@@ -313,7 +338,7 @@ struct Impl {
     static const Ops *ops()
     {
         static const Ops o = {&init,      &step,       &read,         &reduce,      &pjump,
-                              &probe,     &step_smem,  &has_v2,       &batch_member_bytes,
+                              &probe,     &step_smem,  &has_v2,       &pack,        &batch_member_bytes,
                               &batch_items, &batch_fill, &batch_grid, &batch_launch};
         return &o;
     }

@@ -166,6 +166,39 @@ __device__ __forceinline__ void stencil_pairs(At &&at, uint32_t mask, R f0, R fs
     lap = (s - R(1.0 - L::w(0)) * f0) * R(6);
 }
 
+// Velocity gradient gu[a][b] = d_b u_a from packed (u, P) words, per pair as
+// in stencil_pairs; a solid/outside neighbour contributes u = 0.
+template <class L, bool MASKED, class At>
+__device__ __forceinline__ void stencil_u_packed(At &&at, uint32_t mask, float (&gu)[3][3])
+{
+    static_for<0, 3>([&](auto A) {
+        constexpr int a = decltype(A)::value;
+        gu[a][0] = 0.f; gu[a][1] = 0.f; gu[a][2] = 0.f;
+    });
+    static_for<0, (L::Q - 1) / 2>([&](auto Pr) {
+        constexpr int i = 2 * decltype(Pr)::value + 1;
+        const auto I = std::integral_constant<int, i>{};
+        float4 fp = at(I, 1), fm = at(I, -1);
+        if constexpr (MASKED) {
+            if ((mask >> (i + 1)) & 1u) fp = make_float4(0.f, 0.f, 0.f, 0.f);
+            if ((mask >> i) & 1u) fm = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const float wi = float(L::w(i));
+        const float d[3] = {(fp.x - fm.x) * wi, (fp.y - fm.y) * wi, (fp.z - fm.z) * wi};
+        static_for<0, L::D>([&](auto Ax) {
+            constexpr int ax = decltype(Ax)::value;
+            static_for<0, 3>([&](auto B) {
+                constexpr int b = decltype(B)::value;
+                if constexpr (L::c(i, b) != 0) acc_c<L::c(i, b)>(gu[ax][b], d[ax]);
+            });
+        });
+    });
+    static_for<0, 3>([&](auto A) {
+        constexpr int a = decltype(A)::value;
+        gu[a][0] = gu[a][0] * 3.f; gu[a][1] = gu[a][1] * 3.f; gu[a][2] = gu[a][2] * 3.f;
+    });
+}
+
 // Stencil dispatch: pair-summed for FP32 (with a branch for sites without a
 // solid/outside neighbour), canonical for FP64.
 template <class L, class R, class At>

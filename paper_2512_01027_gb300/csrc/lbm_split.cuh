@@ -98,6 +98,10 @@ __device__ __forceinline__ IX write_idx(IX N, const Nbr32 &nb, int idx, uint32_t
     }
 }
 
+// FP32 arithmetic reads and writes (u, P) as packed 16-byte words as well.
+template <class R>
+inline constexpr bool kPacked = std::is_same<R, float>::value;
+
 constexpr int kSplitThreads = 128;
 constexpr int kSplitMinBlocks = 4;   // <= 128 registers a thread: 16 warps an SM
 
@@ -112,7 +116,9 @@ __device__ __forceinline__ void moments_site(const SplitArgs<R, typename C::S> &
     const IX N = (IX)a.N;
     const Nbr32 nb(idx, a.nx, a.ny, D == 3 ? a.nz : 1);
     R hp[Q], gp[Q], Pn[Q], K[Q];
-    const R P0 = a.P_old[idx];
+    R P0;
+    if constexpr (kPacked<R>) P0 = a.F_old[idx].w;
+    else P0 = a.P_old[idx];
     R sum_wcu = R(0);
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
@@ -124,16 +130,23 @@ __device__ __forceinline__ void moments_site(const SplitArgs<R, typename C::S> &
         } else {
             const bool bb = HAS_MASK && ((m >> i) & 1u);
             const int src = nb.at<L, i>(-1);
-            Pn[i] = bb ? P0 : a.P_old[src];
-            if (!bb) {
-                R un[3];
+            R un[3];
+            if constexpr (kPacked<R>) {
+                const float4 f = a.F_old[src];
+                Pn[i] = bb ? P0 : f.w;
+                un[0] = f.x; un[1] = f.y; un[2] = f.z;
+            } else {
+                Pn[i] = bb ? P0 : a.P_old[src];
                 static_for<0, 3>([&](auto A) {
                     constexpr int ax = decltype(A)::value;
-                    if constexpr (ax < D && L::c(i, ax) != 0) un[ax] = a.u_old[eidx<IX>(ax, N, src)];
-                    else un[ax] = R(0);
+                    if constexpr (ax < D && L::c(i, ax) != 0) {
+                        if (!bb) un[ax] = a.u_old[eidx<IX>(ax, N, src)];
+                    } else {
+                        un[ax] = R(0);
+                    }
                 });
-                sum_wcu = sum_wcu + R(L::w(i)) * dot_c<L, i>(un);
             }
+            if (!bb) sum_wcu = sum_wcu + R(L::w(i)) * dot_c<L, i>(un);
         }
     });
     R phi, phihat, rho, u[3], sumg, sumK;
@@ -151,6 +164,7 @@ __device__ __forceinline__ void moments_site(const SplitArgs<R, typename C::S> &
         constexpr int ax = decltype(A)::value;
         a.u_new[eidx<IX>(ax, N, idx)] = u[ax];
     });
+    if constexpr (kPacked<R>) a.F_new[idx] = make_float4(u[0], u[1], D == 3 ? u[2] : 0.f, Pnew);
 }
 
 // S0 + S2..S5 at site idx (0 <= idx < a.N).
@@ -169,18 +183,29 @@ __device__ __forceinline__ void collide_site(const SplitArgs<R, typename C::S> &
     stencil_any<L, R>([&](auto I, int s) { return a.phi[nb.at<L, decltype(I)::value>(s)]; }, m, phi, phi, gphi,
                       lphi);
     R u[3], gu[3][3];
-    u[2] = R(0);
-    gu[0][2] = gu[1][2] = gu[2][0] = gu[2][1] = gu[2][2] = R(0);
-    static_for<0, D>([&](auto A) {
-        constexpr int ax = decltype(A)::value;
-        u[ax] = a.u_new[eidx<IX>(ax, N, idx)];
-        R lap_unused;
-        stencil_any<L, R>([&](auto I, int s) { return a.u_new[eidx<IX>(ax, N, nb.at<L, decltype(I)::value>(s))]; },
-                          m, u[ax], R(0), gu[ax], lap_unused);
-    });
+    R P;
+    if constexpr (kPacked<R>) {
+        const float4 f0 = a.F_new[idx];
+        u[0] = f0.x; u[1] = f0.y; u[2] = f0.z;
+        P = f0.w;
+        auto at = [&](auto I, int s) { return a.F_new[nb.at<L, decltype(I)::value>(s)]; };
+        if (m == 0u) stencil_u_packed<L, false>(at, m, gu);
+        else stencil_u_packed<L, true>(at, m, gu);
+    } else {
+        u[2] = R(0);
+        gu[0][2] = gu[1][2] = gu[2][0] = gu[2][1] = gu[2][2] = R(0);
+        static_for<0, D>([&](auto A) {
+            constexpr int ax = decltype(A)::value;
+            u[ax] = a.u_new[eidx<IX>(ax, N, idx)];
+            R lap_unused;
+            stencil_any<L, R>(
+                [&](auto I, int s) { return a.u_new[eidx<IX>(ax, N, nb.at<L, decltype(I)::value>(s))]; }, m, u[ax],
+                R(0), gu[ax], lap_unused);
+        });
+        P = a.P_new[idx];
+    }
     const R phihat = a.k.clamp ? clamp01(phi) : phi;
     const R rho = a.k.rho_a + phihat * a.k.drho;
-    const R P = a.P_new[idx];
     R hp[Q], gp[Q], hs[Q], gs[Q];
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;

@@ -108,13 +108,15 @@ def test_no_cpu_fallback_without_a_device():
 
 def test_footprint_estimate_needs_no_device():
     """Admission control sizes a lattice before creating it: populations
-    (2 sets in place, 4 ping-pong), P, u (two each), phi, scratch, mask."""
+    (2 sets in place, 4 ping-pong), P, u (two each), phi, packed (u, P)
+    words (two, FP32 arithmetic only), scratch, mask."""
     N = 32 ** 3
     scratch = 8 * (1024 * 8 + 64) + 256
+    packed = 2 * 16 * N
     got = lbm.estimate_footprint("D3Q27", (32, 32, 32), storage="f16", inplace=1)
-    assert got == 2 * 27 * N * 2 + 9 * N * 4 + scratch
+    assert got == 2 * 27 * N * 2 + 9 * N * 4 + packed + scratch
     got = lbm.estimate_footprint("D3Q27", (32, 32, 32), periodic=(1, 1, 0), storage="f32")
-    assert got == 4 * 27 * N * 4 + 9 * N * 4 + scratch + 4 * N
+    assert got == 4 * 27 * N * 4 + 9 * N * 4 + packed + scratch + 4 * N
     got = lbm.estimate_footprint("D2Q9", (16, 8, 1), storage="f64")
     assert got == 4 * 9 * 128 * 8 + 7 * 128 * 8 + scratch
     solid = np.zeros((1, 8, 16), np.uint8)
