@@ -134,7 +134,7 @@ size_t footprint_bytes(int Q, int D, long long N, int storage, bool inplace, boo
     const size_t pop = (size_t)Q * (size_t)N * storage_bytes(storage);
     const size_t field = (size_t)N * compute_bytes(storage);
     size_t s = (inplace ? 2 : 4) * pop + (3 + 2 * (size_t)D) * field + sizeof(double) * kScratchDoubles + 256;
-    if (storage != LBM_STORE_F64) s += 2 * sizeof(float) * 4 * (size_t)N;   // packed (u, P), ping-pong
+    if (storage != LBM_STORE_F64) s += 2 * sizeof(float) * 4 * (size_t)N;   // packed (u, phi), ping-pong
     if (has_mask) s += sizeof(uint32_t) * (size_t)N;
     return s;
 }
@@ -329,7 +329,7 @@ int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params, lbm_
             if (!c->f4[b]) c->phi = nullptr;
         }
     if (!c->phi) {
-        g_create_err = "device allocation of the phi or packed (u, P) fields failed";
+        g_create_err = "device allocation of the phi or packed (u, phi) fields failed";
         release(c);
         delete c;
         return LBM_ERR_OOM;

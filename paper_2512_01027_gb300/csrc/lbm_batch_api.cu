@@ -211,7 +211,7 @@ int lbm_batch_step(lbm_batch b, int64_t n, int *finished)
             if (take[j] > 0) order.push_back((int)j);
         }
         if (order.empty()) break;
-        // packed (u, P) words of members whose state was (re)loaded or fused-stepped
+        // packed velocity words of members whose state was (re)loaded or fused-stepped
         for (int j : order) {
             lbm_ctx *h = b->members[j];
             if (h->f4_valid) continue;

@@ -23,6 +23,7 @@ inline SiteConsts<R> site_consts(const HostConsts &h)
     k.cP = R(h.cP); k.tau_a = R(h.tau_a); k.dtau = R(h.dtau); k.inv_tau_phi = R(h.inv_tau_phi);
     k.lambda_b = R(h.lambda_b); k.M3 = R(h.M3); k.W = R(h.W); k.eps = R(h.eps);
     k.phi_n = R(h.phi_n); k.phi_m = R(h.phi_m); k.D = R(h.D); k.dt_pref = R(h.dt_pref);
+    k.invW = R(1.0 / h.W); k.invD = R(1.0 / h.D);
     k.A_mu = R(h.A_mu); k.B_mu = R(h.B_mu);
     k.g[0] = R(h.g[0]); k.g[1] = R(h.g[1]); k.g[2] = R(h.g[2]);
     k.clamp = h.clamp; k.full_trace = h.full_trace;
@@ -134,14 +135,13 @@ struct Impl {
         return steps % 2 == 0 ? kAAOdd : kAAEven;
     }
 
-    // Packed (u, P) words of the current state, when they are stale.
+    // Packed velocity words of the current state, when they are stale.
     static int pack(lbm_ctx *c)
     {
         if constexpr (kPacked<R>) {
             if (c->f4_valid || !c->f4[c->cur]) return LBM_OK;
             const unsigned blocks = (unsigned)((c->N + 255) / 256);
-            pack_kernel<L::D><<<blocks, 256, 0, c->stream>>>(static_cast<const float *>(c->P[c->cur]),
-                                                             static_cast<const float *>(c->u[c->cur]),
+            pack_kernel<L::D><<<blocks, 256, 0, c->stream>>>(static_cast<const float *>(c->u[c->cur]),
                                                              static_cast<float4 *>(c->f4[c->cur]), c->N);
             const int rc = cuda_fail(c, cudaGetLastError(), "pack_kernel launch");
             if (rc == LBM_OK) c->f4_valid = true;

@@ -57,8 +57,8 @@ struct lbm_ctx {
     void *P[2] = {nullptr, nullptr};
     void *u[2] = {nullptr, nullptr};
     void *phi = nullptr;           // phi^{n+1} of the split form [N]
-    void *f4[2] = {nullptr, nullptr};   // packed (u, P) per site, FP32 arithmetic (follows P, u)
-    bool f4_valid = false;         // f4[cur] mirrors P[cur], u[cur]
+    void *f4[2] = {nullptr, nullptr};   // packed (u, phi) per site, FP32 arithmetic (follows u)
+    bool f4_valid = false;         // f4[cur] holds u[cur]
     bool inplace = false;          // one population store, AA streaming
     uint32_t *mask = nullptr;
     int *d_err = nullptr;
@@ -110,7 +110,7 @@ struct Ops {
     int (*probe)(lbm_ctx *c, const long long *d_sites, int n, double *d_h, double *d_g, double *d_P, double *d_u);
     size_t (*step_smem)();
     bool (*has_v2)();
-    int (*pack)(lbm_ctx *c);       // f4[cur] from P[cur], u[cur] (no-op without packed words)
+    int (*pack)(lbm_ctx *c);       // f4[cur] from u[cur] (no-op without packed words)
     // batched persistent launch (lbm_batch_*)
     size_t (*batch_member_bytes)();
     long long (*batch_items)(const lbm_ctx *c);

@@ -33,6 +33,7 @@ struct SiteConsts {
     R W;
     R eps;
     R phi_n, phi_m, D;
+    R invW, invD;   // 1 / W, 1 / D (the FP32 forms multiply by them)
     R dt_pref;      // gamma M / (T W)
     R A_mu;         // 48 sigma / W
     R B_mu;         // 3 sigma W / 2
@@ -166,37 +167,47 @@ __device__ __forceinline__ void stencil_pairs(At &&at, uint32_t mask, R f0, R fs
     lap = (s - R(1.0 - L::w(0)) * f0) * R(6);
 }
 
-// Velocity gradient gu[a][b] = d_b u_a from packed (u, P) words, per pair as
-// in stencil_pairs; a solid/outside neighbour contributes u = 0.
+// Gradient and Laplacian of phi and velocity gradient gu[a][b] = d_b u_a
+// from packed (u, phi) words, per pair as in stencil_pairs.  A solid or
+// outside neighbour contributes phi = phi(x) and u = 0.
 template <class L, bool MASKED, class At>
-__device__ __forceinline__ void stencil_u_packed(At &&at, uint32_t mask, float (&gu)[3][3])
+__device__ __forceinline__ void stencil_packed(At &&at, uint32_t mask, float phi0, float (&gphi)[3], float &lphi,
+                                               float (&gu)[3][3])
 {
     static_for<0, 3>([&](auto A) {
         constexpr int a = decltype(A)::value;
         gu[a][0] = 0.f; gu[a][1] = 0.f; gu[a][2] = 0.f;
+        gphi[a] = 0.f;
     });
+    float sphi = 0.f;
     static_for<0, (L::Q - 1) / 2>([&](auto Pr) {
         constexpr int i = 2 * decltype(Pr)::value + 1;
         const auto I = std::integral_constant<int, i>{};
         float4 fp = at(I, 1), fm = at(I, -1);
         if constexpr (MASKED) {
-            if ((mask >> (i + 1)) & 1u) fp = make_float4(0.f, 0.f, 0.f, 0.f);
-            if ((mask >> i) & 1u) fm = make_float4(0.f, 0.f, 0.f, 0.f);
+            if ((mask >> (i + 1)) & 1u) fp = make_float4(0.f, 0.f, 0.f, phi0);
+            if ((mask >> i) & 1u) fm = make_float4(0.f, 0.f, 0.f, phi0);
         }
         const float wi = float(L::w(i));
-        const float d[3] = {(fp.x - fm.x) * wi, (fp.y - fm.y) * wi, (fp.z - fm.z) * wi};
-        static_for<0, L::D>([&](auto Ax) {
-            constexpr int ax = decltype(Ax)::value;
-            static_for<0, 3>([&](auto B) {
-                constexpr int b = decltype(B)::value;
-                if constexpr (L::c(i, b) != 0) acc_c<L::c(i, b)>(gu[ax][b], d[ax]);
-            });
+        const float d[4] = {(fp.x - fm.x) * wi, (fp.y - fm.y) * wi, (fp.z - fm.z) * wi, (fp.w - fm.w) * wi};
+        static_for<0, 3>([&](auto B) {
+            constexpr int b = decltype(B)::value;
+            if constexpr (L::c(i, b) != 0) {
+                acc_c<L::c(i, b)>(gphi[b], d[3]);
+                static_for<0, L::D>([&](auto Ax) {
+                    constexpr int ax = decltype(Ax)::value;
+                    acc_c<L::c(i, b)>(gu[ax][b], d[ax]);
+                });
+            }
         });
+        sphi = sphi + (fp.w + fm.w) * wi;
     });
     static_for<0, 3>([&](auto A) {
         constexpr int a = decltype(A)::value;
         gu[a][0] = gu[a][0] * 3.f; gu[a][1] = gu[a][1] * 3.f; gu[a][2] = gu[a][2] * 3.f;
+        gphi[a] = gphi[a] * 3.f;
     });
+    lphi = (sphi - float(1.0 - L::w(0)) * phi0) * 6.f;
 }
 
 // Stencil dispatch: pair-summed for FP32 (with a branch for sites without a
@@ -303,6 +314,178 @@ __device__ __forceinline__ R s1_pressure(const SiteConsts<R> &k, const R *gp, co
     else return k.rhoref_T * s + omega * k.rho_a * sum_wcu;
 }
 
+// S3..S5 of one site in FP32, per direction pair.  For the pair (c, -c),
+// h_eq and g_eq split into a part even in c and a part odd in c:
+//   h_eq(+-c) = w { phi (1 - u^2/(2T)) + phi (c.u)^2/(2T^2) } +- w c.(phi u/T + theta n)
+//   g_eq(+-c) = w { (c.u)^2/(2T^2) - u^2/(2T) + B div/T } +- w c.(u/T + F/(rho T) + sigma grad rho/(rho^2 T))
+// so each pair needs one c.u and two dot products with per-site vectors.
+// The same formulas as the canonical collide below, regrouped; divisions by
+// per-site quantities become one reciprocal each.
+template <class L, bool INIT, bool PDEV>
+__device__ __forceinline__ void collide_pairs(const SiteConsts<float> &k, float phi, float phihat, float rho,
+                                              float P, const float (&u)[3], const float (&gphi)[3], float lphi,
+                                              const float (&gu)[3][3], const float *hp, const float *gp, float *hs,
+                                              float *gs)
+{
+    constexpr int D = L::D;
+    constexpr int NP = (L::Q - 1) / 2;
+    // --- S3
+    float gg = gphi[0] * gphi[0] + gphi[1] * gphi[1];
+    if constexpr (D == 3) gg = gg + gphi[2] * gphi[2];
+    const float gnorm = sqrtf(gg);
+    const float ninv = 1.f / (gnorm + k.eps);
+    float n[3];
+    n[0] = gphi[0] * ninv;
+    n[1] = gphi[1] * ninv;
+    n[2] = (D == 3) ? gphi[2] * ninv : 0.f;
+    const float theta = k.M3 * ((1.f - 4.f * (phi - 0.5f) * (phi - 0.5f)) * k.invW);
+    float dtheta;
+    {
+        const float s = lphi / (fabsf(lphi) + k.eps);
+        const float Y1 = fminf(fmaxf(0.f, fminf(1.f, (phi - k.phi_n) * k.invD)),
+                               fmaxf(0.f, fminf(1.f, (1.f - phi) * k.invD)));
+        const float Y2 = fminf(fmaxf(0.f, fminf(1.f, phi * k.invD)),
+                               fmaxf(0.f, fminf(1.f, (k.phi_m - phi) * k.invD)));
+        dtheta = k.dt_pref * gnorm * ((1.f + s) * Y1 + (1.f - s) * Y2);
+    }
+    const float theta_tot = theta + dtheta;
+    const float mu = k.A_mu * phi * (phi - 1.f) * (phi - 0.5f) - k.B_mu * lphi;
+    float F[3];
+    F[0] = rho * k.g[0] + mu * gphi[0];
+    F[1] = rho * k.g[1] + mu * gphi[1];
+    F[2] = (D == 3) ? rho * k.g[2] + mu * gphi[2] : 0.f;
+    const float tau = k.tau_a + phihat * k.dtau;
+    const float nu = (tau - 0.5f) * (1.f / 3.f);
+    const float B = (2.f / 3.f) * (nu - k.lambda_b) + (1.f / 6.f);
+    float div = gu[0][0] + gu[1][1];
+    if constexpr (D == 3) div = div + gu[2][2];
+    float grho[3];
+    grho[0] = k.drho * gphi[0];
+    grho[1] = k.drho * gphi[1];
+    grho[2] = (D == 3) ? k.drho * gphi[2] : 0.f;
+    float sg[3];
+    {
+        const float rnu = rho * nu;
+        const float bulk = rho * (2.f / 3.f) * (k.lambda_b - nu) * div;
+        float sig[3][3];
+        static_for<0, D>([&](auto A) {
+            constexpr int a = decltype(A)::value;
+            static_for<0, D>([&](auto Bb) {
+                constexpr int b = decltype(Bb)::value;
+                if constexpr (a == b) sig[a][b] = rnu * (gu[a][b] + gu[b][a]) + bulk;
+                else sig[a][b] = rnu * (gu[a][b] + gu[b][a]);
+            });
+        });
+        static_for<0, D>([&](auto A) {
+            constexpr int l = decltype(A)::value;
+            float t = sig[l][0] * grho[0] + sig[l][1] * grho[1];
+            if constexpr (D == 3) t = t + sig[l][2] * grho[2];
+            sg[l] = t;
+        });
+        if constexpr (D == 2) sg[2] = 0.f;
+    }
+    float uu = u[0] * u[0] + u[1] * u[1];
+    if constexpr (D == 3) uu = uu + u[2] * u[2];
+
+    // per-site parts of the equilibria
+    const float rinv = 1.f / rho;
+    const float kF = 3.f * rinv;          // 1 / (rho T)
+    const float kS = kF * rinv;           // 1 / (rho^2 T)
+    const float bdiv = B * div * 3.f;     // B div / T
+    float Vh[3], Vg[3];
+    static_for<0, 3>([&](auto A) {
+        constexpr int a = decltype(A)::value;
+        Vh[a] = 3.f * phi * u[a] + theta_tot * n[a];
+        Vg[a] = 3.f * u[a] + F[a] * kF + sg[a] * kS;
+    });
+    const float Eh0 = phi * (1.f - 1.5f * uu);
+    const float Eg0 = bdiv - 1.5f * uu;
+    const float p45 = 4.5f * phi;
+
+    // --- S4 and S5, rest direction
+    const float w0 = float(L::w(0));
+    const float heq0 = w0 * Eh0;
+    float geq0 = w0 * (-1.5f * uu) + (w0 - 1.f) * bdiv;
+    if constexpr (!PDEV) geq0 = P * k.cP + geq0;
+    if constexpr (INIT) {
+        hs[0] = heq0;
+        gs[0] = geq0;
+    } else {
+        hs[0] = hp[0] - (hp[0] - heq0) * k.inv_tau_phi;
+    }
+    float eg[NP], og[NP], ne[NP];
+    static_for<0, NP>([&](auto Pp) {
+        constexpr int p = decltype(Pp)::value;
+        constexpr int i = 2 * p + 1;
+        const float wi = float(L::w(i));
+        const float cu = dot_c<L, i>(u);
+        const float cu2 = cu * cu;
+        const float eh = wi * (Eh0 + p45 * cu2);
+        const float oh = wi * dot_c<L, i>(Vh);
+        eg[p] = wi * (Eg0 + 4.5f * cu2);
+        og[p] = wi * dot_c<L, i>(Vg);
+        if constexpr (INIT) {
+            hs[i] = eh + oh;
+            hs[i + 1] = eh - oh;
+            gs[i] = eg[p] + og[p];
+            gs[i + 1] = eg[p] - og[p];
+        } else {
+            hs[i] = hp[i] - (hp[i] - (eh + oh)) * k.inv_tau_phi;
+            hs[i + 1] = hp[i + 1] - (hp[i + 1] - (eh - oh)) * k.inv_tau_phi;
+            ne[p] = (gp[i] + gp[i + 1]) - 2.f * eg[p];   // (g - g_eq) summed over the pair
+        }
+    });
+    if constexpr (!INIT) {
+        // Pi_ab = sum_k c_ka c_kb (g_k - g_eq_k), per pair (c_ka c_kb is even in c)
+        float Pi[3][3];
+        static_for<0, D>([&](auto A) {
+            constexpr int a = decltype(A)::value;
+            static_for<a, D>([&](auto Bb) {
+                constexpr int b = decltype(Bb)::value;
+                float acc = 0.f;
+                static_for<0, NP>([&](auto Pp) {
+                    constexpr int p = decltype(Pp)::value;
+                    constexpr int cc = L::c(2 * p + 1, a) * L::c(2 * p + 1, b);
+                    if constexpr (cc != 0) acc_c<cc>(acc, ne[p]);
+                });
+                Pi[a][b] = acc;
+                if constexpr (a != b) Pi[b][a] = acc;
+            });
+        });
+        float tr = Pi[0][0] + Pi[1][1];
+        if constexpr (D == 3) tr = tr + Pi[2][2];
+        if (!k.full_trace) {
+            const float trd = tr * (1.f / float(D));
+            static_for<0, D>([&](auto A) {
+                constexpr int a = decltype(A)::value;
+                Pi[a][a] = Pi[a][a] - trd;
+            });
+            tr = 0.f;
+        }
+        // (c_ia c_ib - T delta_ab) Pi_ab = c_ia c_ib Pi_ab - T tr Pi, the same for c and -c
+        const float om = 1.f - 1.f / tau;
+        const float base = -(1.f / 3.f) * tr;
+        gs[0] = geq0 + om * (w0 * 4.5f) * base;
+        static_for<0, NP>([&](auto Pp) {
+            constexpr int p = decltype(Pp)::value;
+            constexpr int i = 2 * p + 1;
+            float contr = base;
+            static_for<0, D>([&](auto A) {
+                constexpr int a = decltype(A)::value;
+                if constexpr (L::c(i, a) != 0) contr = contr + Pi[a][a];
+                static_for<a + 1, D>([&](auto Bb) {
+                    constexpr int b = decltype(Bb)::value;
+                    constexpr int cc = L::c(i, a) * L::c(i, b);
+                    if constexpr (cc != 0) acc_c<cc>(contr, 2.f * Pi[a][b]);
+                });
+            });
+            const float e = eg[p] + om * (float(L::w(i)) * 4.5f) * contr;
+            gs[i] = e + og[p];
+            gs[i + 1] = e - og[p];
+        });
+    }
+}
+
 // S3..S5 of one site: from phi, phihat, rho, P = P^{n+1}, u = u^{n+1}, the
 // stencils and the pulled populations (hp, gp), the post-collision
 // populations hs, gs.  INIT: return the equilibria (start state).
@@ -313,6 +496,10 @@ __device__ __forceinline__ void collide(const SiteConsts<R> &k, R phi, R phihat,
                                         const R (&gphi)[3], R lphi, const R (&gu)[3][3], const R *hp,
                                         const R *gp, R *hs, R *gs)
 {
+    if constexpr (kPairForms<R>) {
+        collide_pairs<L, INIT, PDEV>(k, phi, phihat, rho, P, u, gphi, lphi, gu, hp, gp, hs, gs);
+        return;
+    }
     constexpr int D = L::D;
     // --- S3: normal, theta, delta-theta, chemical potential, force
     R gg = gphi[0] * gphi[0] + gphi[1] * gphi[1];
@@ -404,58 +591,6 @@ __device__ __forceinline__ void collide(const SiteConsts<R> &k, R phi, R phihat,
     if constexpr (INIT) {
         static_for<0, L::Q>([&](auto I) { gs[decltype(I)::value] = geq[decltype(I)::value]; });
         return;
-    } else if constexpr (kPairForms<R>) {
-        // Pi_ab = sum_k c_ka c_kb (g_k - g_eq_k), per pair (c_ka c_kb is even in c)
-        R ne[(L::Q - 1) / 2];
-        static_for<0, (L::Q - 1) / 2>([&](auto Pp) {
-            constexpr int p = decltype(Pp)::value;
-            ne[p] = (gp[2 * p + 1] - geq[2 * p + 1]) + (gp[2 * p + 2] - geq[2 * p + 2]);
-        });
-        R Pi[3][3];
-        static_for<0, D>([&](auto A) {
-            constexpr int a = decltype(A)::value;
-            static_for<a, D>([&](auto Bb) {
-                constexpr int b = decltype(Bb)::value;
-                R acc = R(0);
-                static_for<0, (L::Q - 1) / 2>([&](auto Pp) {
-                    constexpr int p = decltype(Pp)::value;
-                    constexpr int cc = L::c(2 * p + 1, a) * L::c(2 * p + 1, b);
-                    if constexpr (cc != 0) acc_c<cc>(acc, ne[p]);
-                });
-                Pi[a][b] = acc;
-                if constexpr (a != b) Pi[b][a] = acc;
-            });
-        });
-        R tr = Pi[0][0] + Pi[1][1];
-        if constexpr (D == 3) tr = tr + Pi[2][2];
-        if (!k.full_trace) {
-            const R trd = tr / R(D);
-            static_for<0, D>([&](auto A) {
-                constexpr int a = decltype(A)::value;
-                Pi[a][a] = Pi[a][a] - trd;
-            });
-            tr = R(0);
-        }
-        // (c_ia c_ib - T delta_ab) Pi_ab = c_ia c_ib Pi_ab - T tr Pi, the same for i and -i
-        const R om = R(1) - R(1) / tau;
-        const R base = -R(1.0 / 3.0) * tr;
-        gs[0] = geq[0] + om * (R(L::w(0)) * R(4.5)) * base;
-        static_for<0, (L::Q - 1) / 2>([&](auto Pp) {
-            constexpr int i = 2 * decltype(Pp)::value + 1;
-            R contr = base;
-            static_for<0, D>([&](auto A) {
-                constexpr int a = decltype(A)::value;
-                if constexpr (L::c(i, a) != 0) contr = contr + Pi[a][a];
-                static_for<a + 1, D>([&](auto Bb) {
-                    constexpr int b = decltype(Bb)::value;
-                    constexpr int cc = L::c(i, a) * L::c(i, b);
-                    if constexpr (cc != 0) acc_c<cc>(contr, R(2) * Pi[a][b]);
-                });
-            });
-            const R f = om * (R(L::w(i)) * R(4.5)) * contr;
-            gs[i] = geq[i] + f;
-            gs[i + 1] = geq[i + 1] + f;
-        });
     } else {
         // Pi_ab = sum_k c_ka c_kb (g_k - g_eq_k)
         R Pi[3][3];

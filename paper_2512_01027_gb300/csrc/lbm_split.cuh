@@ -98,7 +98,9 @@ __device__ __forceinline__ IX write_idx(IX N, const Nbr32 &nb, int idx, uint32_t
     }
 }
 
-// FP32 arithmetic reads and writes (u, P) as packed 16-byte words as well.
+// FP32 arithmetic also keeps (u, phi) of each site as one packed 16-byte
+// word: the moments launch reads a neighbour's velocity with one load, the
+// collision launch its velocity and phi.
 template <class R>
 inline constexpr bool kPacked = std::is_same<R, float>::value;
 
@@ -116,9 +118,7 @@ __device__ __forceinline__ void moments_site(const SplitArgs<R, typename C::S> &
     const IX N = (IX)a.N;
     const Nbr32 nb(idx, a.nx, a.ny, D == 3 ? a.nz : 1);
     R hp[Q], gp[Q], Pn[Q], K[Q];
-    R P0;
-    if constexpr (kPacked<R>) P0 = a.F_old[idx].w;
-    else P0 = a.P_old[idx];
+    const R P0 = a.P_old[idx];
     R sum_wcu = R(0);
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
@@ -133,7 +133,7 @@ __device__ __forceinline__ void moments_site(const SplitArgs<R, typename C::S> &
             R un[3];
             if constexpr (kPacked<R>) {
                 const float4 f = a.F_old[src];
-                Pn[i] = bb ? P0 : f.w;
+                Pn[i] = bb ? P0 : a.P_old[src];
                 un[0] = f.x; un[1] = f.y; un[2] = f.z;
             } else {
                 Pn[i] = bb ? P0 : a.P_old[src];
@@ -158,13 +158,13 @@ __device__ __forceinline__ void moments_site(const SplitArgs<R, typename C::S> &
         s1_moments<L, R>(a.k, hp, gp, Pn, P0, phi, phihat, rho, u, K);
         Pnew = s1_pressure<L, R, C::kPdev>(a.k, gp, K, rho, sum_wcu, P0);
     }
-    a.phi[idx] = phi;
     a.P_new[idx] = Pnew;
     static_for<0, D>([&](auto A) {
         constexpr int ax = decltype(A)::value;
         a.u_new[eidx<IX>(ax, N, idx)] = u[ax];
     });
-    if constexpr (kPacked<R>) a.F_new[idx] = make_float4(u[0], u[1], D == 3 ? u[2] : 0.f, Pnew);
+    if constexpr (kPacked<R>) a.F_new[idx] = make_float4(u[0], u[1], D == 3 ? u[2] : 0.f, phi);
+    else a.phi[idx] = phi;
 }
 
 // S0 + S2..S5 at site idx (0 <= idx < a.N).
@@ -178,20 +178,20 @@ __device__ __forceinline__ void collide_site(const SplitArgs<R, typename C::S> &
     const IX N = (IX)a.N;
     const Nbr32 nb(idx, a.nx, a.ny, D == 3 ? a.nz : 1);
     // S2: stencils of phi^{n+1} and u^{n+1} from the fields of the moments launch
-    const R phi = a.phi[idx];
-    R gphi[3], lphi;
-    stencil_any<L, R>([&](auto I, int s) { return a.phi[nb.at<L, decltype(I)::value>(s)]; }, m, phi, phi, gphi,
-                      lphi);
+    R phi, gphi[3], lphi;
     R u[3], gu[3][3];
-    R P;
+    const R P = a.P_new[idx];
     if constexpr (kPacked<R>) {
         const float4 f0 = a.F_new[idx];
         u[0] = f0.x; u[1] = f0.y; u[2] = f0.z;
-        P = f0.w;
+        phi = f0.w;
         auto at = [&](auto I, int s) { return a.F_new[nb.at<L, decltype(I)::value>(s)]; };
-        if (m == 0u) stencil_u_packed<L, false>(at, m, gu);
-        else stencil_u_packed<L, true>(at, m, gu);
+        if (m == 0u) stencil_packed<L, false>(at, m, phi, gphi, lphi, gu);
+        else stencil_packed<L, true>(at, m, phi, gphi, lphi, gu);
     } else {
+        phi = a.phi[idx];
+        stencil_any<L, R>([&](auto I, int s) { return a.phi[nb.at<L, decltype(I)::value>(s)]; }, m, phi, phi, gphi,
+                          lphi);
         u[2] = R(0);
         gu[0][2] = gu[1][2] = gu[2][0] = gu[2][1] = gu[2][2] = R(0);
         static_for<0, D>([&](auto A) {
@@ -202,7 +202,6 @@ __device__ __forceinline__ void collide_site(const SplitArgs<R, typename C::S> &
                 [&](auto I, int s) { return a.u_new[eidx<IX>(ax, N, nb.at<L, decltype(I)::value>(s))]; }, m, u[ax],
                 R(0), gu[ax], lap_unused);
         });
-        P = a.P_new[idx];
     }
     const R phihat = a.k.clamp ? clamp01(phi) : phi;
     const R rho = a.k.rho_a + phihat * a.k.drho;

@@ -108,7 +108,7 @@ def test_no_cpu_fallback_without_a_device():
 
 def test_footprint_estimate_needs_no_device():
     """Admission control sizes a lattice before creating it: populations
-    (2 sets in place, 4 ping-pong), P, u (two each), phi, packed (u, P)
+    (2 sets in place, 4 ping-pong), P, u (two each), phi, packed (u, phi)
     words (two, FP32 arithmetic only), scratch, mask."""
     N = 32 ** 3
     scratch = 8 * (1024 * 8 + 64) + 256
