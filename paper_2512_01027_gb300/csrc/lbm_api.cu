@@ -134,7 +134,8 @@ size_t footprint_bytes(int Q, int D, long long N, int storage, bool inplace, boo
     const size_t pop = (size_t)Q * (size_t)N * storage_bytes(storage);
     const size_t field = (size_t)N * compute_bytes(storage);
     size_t s = (inplace ? 2 : 4) * pop + (3 + 2 * (size_t)D) * field + sizeof(double) * kScratchDoubles + 256;
-    if (storage != LBM_STORE_F64) s += 2 * sizeof(float) * 4 * (size_t)N;   // packed (u, phi), ping-pong
+    // FP32 arithmetic: packed (u, P) ping-pong, packed (u, phi), second moments of g
+    if (storage != LBM_STORE_F64) s += (2 * 16 + 16 + 4 * (D == 3 ? 6 : 3)) * (size_t)N;
     if (has_mask) s += sizeof(uint32_t) * (size_t)N;
     return s;
 }
@@ -323,13 +324,15 @@ int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params, lbm_
         }
     }
     c->phi = own(c, c->field_bytes);
-    if (storage != LBM_STORE_F64)
-        for (int b = 0; b < 2 && c->phi; ++b) {
-            c->f4[b] = own(c, sizeof(float) * 4 * (size_t)N);
-            if (!c->f4[b]) c->phi = nullptr;
-        }
+    if (storage != LBM_STORE_F64 && c->phi) {
+        c->fa[0] = own(c, 16 * (size_t)N);
+        c->fa[1] = own(c, 16 * (size_t)N);
+        c->fb = own(c, 16 * (size_t)N);
+        c->pig = own(c, 4 * (size_t)(D == 3 ? 6 : 3) * (size_t)N);
+        if (!c->fa[0] || !c->fa[1] || !c->fb || !c->pig) c->phi = nullptr;
+    }
     if (!c->phi) {
-        g_create_err = "device allocation of the phi or packed (u, phi) fields failed";
+        g_create_err = "device allocation of the phi field or the packed words failed";
         release(c);
         delete c;
         return LBM_ERR_OOM;
@@ -569,6 +572,7 @@ int lbm_save_state(lbm_handle h, void *host_buf, size_t bytes)
     const StateHeader hd = state_header(h);
     std::memcpy(p, &hd, sizeof hd);
     p += sizeof hd;
+    if (const int rs = h->ops->sync_soa(h); rs != LBM_OK) return rs;
     const int b = h->cur;
     int rc = cuda_fail(h, cudaMemcpyAsync(p, h->h[b], h->pop_bytes, cudaMemcpyDeviceToHost, h->stream), "D2H state");
     p += h->pop_bytes;
@@ -606,7 +610,8 @@ int lbm_load_state(lbm_handle h, const void *host_buf, size_t bytes)
     if (rc == LBM_OK) rc = cuda_fail(h, cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream), "cudaMemsetAsync(err)");
     if (rc == LBM_OK) rc = cuda_fail(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     if (rc == LBM_OK) std::memcpy(&h->steps, p, sizeof(int64_t));
-    h->f4_valid = false;
+    h->fa_valid = false;
+    h->soa_valid = true;
     return rc;
 }
 

@@ -211,10 +211,10 @@ int lbm_batch_step(lbm_batch b, int64_t n, int *finished)
             if (take[j] > 0) order.push_back((int)j);
         }
         if (order.empty()) break;
-        // packed velocity words of members whose state was (re)loaded or fused-stepped
+        // packed state words of members whose state was (re)loaded or fused-stepped
         for (int j : order) {
             lbm_ctx *h = b->members[j];
-            if (h->f4_valid) continue;
+            if (h->fa_valid) continue;
             rc = b->ops->pack(h);
             if (rc == LBM_OK) rc = bcuda(b, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize(member)");
             if (rc != LBM_OK) {
@@ -257,6 +257,7 @@ int lbm_batch_step(lbm_batch b, int64_t n, int *finished)
             lbm_ctx *h = b->members[j];
             h->steps += take[j];
             if (take[j] & 1) h->cur = 1 - h->cur;
+            if (h->storage != LBM_STORE_F64) h->soa_valid = false;   // the state is in fa[cur]
             b->remaining[j] -= take[j];
         }
         n -= K;

@@ -115,8 +115,10 @@ struct Impl {
         a.k = site_consts<R>(c->consts);
         a.phi = static_cast<R *>(c->phi);
         const int src = c->cur ^ flip, dst = 1 - src;
-        a.F_old = static_cast<const float4 *>(c->f4[src]);
-        a.F_new = static_cast<float4 *>(c->f4[dst]);
+        a.F_old = static_cast<const float4 *>(c->fa[src]);
+        a.F_new = static_cast<float4 *>(c->fa[dst]);
+        a.FB = static_cast<float4 *>(c->fb);
+        a.PiG = static_cast<float *>(c->pig);
         a.src_h = static_cast<const S *>(c->h[src]);
         a.src_g = static_cast<const S *>(c->g[src]);
         a.dst_h = static_cast<S *>(c->h[dst]);
@@ -135,16 +137,34 @@ struct Impl {
         return steps % 2 == 0 ? kAAOdd : kAAEven;
     }
 
-    // Packed velocity words of the current state, when they are stale.
+    // Packed (u, P) words of the current state, when they are stale.
     static int pack(lbm_ctx *c)
     {
         if constexpr (kPacked<R>) {
-            if (c->f4_valid || !c->f4[c->cur]) return LBM_OK;
+            if (c->fa_valid || !c->fa[c->cur]) return LBM_OK;
             const unsigned blocks = (unsigned)((c->N + 255) / 256);
-            pack_kernel<L::D><<<blocks, 256, 0, c->stream>>>(static_cast<const float *>(c->u[c->cur]),
-                                                             static_cast<float4 *>(c->f4[c->cur]), c->N);
+            pack_kernel<L::D><<<blocks, 256, 0, c->stream>>>(static_cast<const float *>(c->P[c->cur]),
+                                                             static_cast<const float *>(c->u[c->cur]),
+                                                             static_cast<float4 *>(c->fa[c->cur]), c->N);
             const int rc = cuda_fail(c, cudaGetLastError(), "pack_kernel launch");
-            if (rc == LBM_OK) c->f4_valid = true;
+            if (rc == LBM_OK) c->fa_valid = true;
+            return rc;
+        } else {
+            return LBM_OK;
+        }
+    }
+
+    // The planes P[cur], u[cur] from the packed words, when they are stale.
+    static int sync_soa(lbm_ctx *c)
+    {
+        if constexpr (kPacked<R>) {
+            if (c->soa_valid) return LBM_OK;
+            const unsigned blocks = (unsigned)((c->N + 255) / 256);
+            unpack_kernel<L::D><<<blocks, 256, 0, c->stream>>>(static_cast<const float4 *>(c->fa[c->cur]), c->mask,
+                                                               static_cast<float *>(c->P[c->cur]),
+                                                               static_cast<float *>(c->u[c->cur]), c->N);
+            const int rc = cuda_fail(c, cudaGetLastError(), "unpack_kernel launch");
+            if (rc == LBM_OK) c->soa_valid = true;
             return rc;
         } else {
             return LBM_OK;
@@ -167,6 +187,7 @@ struct Impl {
             if (rc != LBM_OK) return rc;
             c->cur = 1 - c->cur;
             c->steps += 1;
+            if constexpr (kPacked<R>) c->soa_valid = false;   // the state is in fa[cur]
         }
         return LBM_OK;
     }
@@ -218,6 +239,10 @@ struct Impl {
     static int step(lbm_ctx *c, int64_t n)
     {
         if (c->inplace || c->variant == 3 || c->variant == 0) return step_split(c, n);
+        if (n > 0) {
+            const int rc = sync_soa(c);
+            if (rc != LBM_OK) return rc;
+        }
         StepArgs<R, S> a;
         a.mask = c->mask;
         a.err = c->d_err;
@@ -242,7 +267,7 @@ struct Impl {
             if (rc != LBM_OK) return rc;
             c->cur = dst;
             c->steps += 1;
-            c->f4_valid = false;   // the fused kernels do not write the packed words
+            c->fa_valid = false;   // the fused kernels keep the state in P, u only
         }
         return LBM_OK;
     }
@@ -266,7 +291,8 @@ struct Impl {
         else init_kernel<L, R, C, false><<<blocks, threads, 0, c->stream>>>(a);
         c->cur = 0;
         c->steps = 0;
-        c->f4_valid = false;
+        c->fa_valid = false;
+        c->soa_valid = true;
         return cuda_fail(c, cudaGetLastError(), "init_kernel launch");
     }
 
@@ -288,6 +314,7 @@ struct Impl {
 
     static int read(lbm_ctx *c, double *d_phi, double *d_P, double *d_u, double *d_hpop, double *d_gpop)
     {
+        if (const int rs = sync_soa(c); rs != LBM_OK) return rs;
         ReadArgs<R, S> a = read_args(c);
         a.phi_out = d_phi; a.P_out = d_P; a.u_out = d_u; a.hpop_out = d_hpop; a.gpop_out = d_gpop;
         const int threads = 256;
@@ -299,6 +326,7 @@ struct Impl {
 
     static int reduce(lbm_ctx *c, double *d_out5)
     {
+        if (const int rs = sync_soa(c); rs != LBM_OK) return rs;
         ReadArgs<R, S> a = read_args(c);
         const int blocks = (int)std::min<long long>(kRedMaxBlocks, (c->N + kRedThreads - 1) / kRedThreads);
         double *partials = c->d_scratch;
@@ -314,6 +342,7 @@ struct Impl {
 
     static int pjump(lbm_ctx *c, const double center[3], double r_in, double r_out, double *d_out4)
     {
+        if (const int rs = sync_soa(c); rs != LBM_OK) return rs;
         const int blocks = (int)std::min<long long>(kRedMaxBlocks, (c->N + kRedThreads - 1) / kRedThreads);
         double *partials = c->d_scratch;
         const R *P = static_cast<const R *>(c->P[c->cur]);
@@ -329,6 +358,7 @@ struct Impl {
 
     static int probe(lbm_ctx *c, const long long *d_sites, int n, double *d_h, double *d_g, double *d_P, double *d_u)
     {
+        if (const int rs = sync_soa(c); rs != LBM_OK) return rs;
         ReadArgs<R, S> a = read_args(c);
         const int threads = 128;
         probe_kernel<L, R, C><<<(n + threads - 1) / threads, threads, 0, c->stream>>>(a, d_sites, n, d_h, d_g, d_P, d_u);
@@ -338,7 +368,8 @@ struct Impl {
     static const Ops *ops()
     {
         static const Ops o = {&init,      &step,       &read,         &reduce,      &pjump,
-                              &probe,     &step_smem,  &has_v2,       &pack,        &batch_member_bytes,
+                              &probe,     &step_smem,  &has_v2,       &pack,        &sync_soa,
+                              &batch_member_bytes,
                               &batch_items, &batch_fill, &batch_grid, &batch_launch};
         return &o;
     }

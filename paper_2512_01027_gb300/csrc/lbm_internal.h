@@ -57,8 +57,15 @@ struct lbm_ctx {
     void *P[2] = {nullptr, nullptr};
     void *u[2] = {nullptr, nullptr};
     void *phi = nullptr;           // phi^{n+1} of the split form [N]
-    void *f4[2] = {nullptr, nullptr};   // packed (u, phi) per site, FP32 arithmetic (follows u)
-    bool f4_valid = false;         // f4[cur] holds u[cur]
+    // FP32 arithmetic: during split stepping the state P, u lives in packed
+    // (u, P) words fa[cur]; fb holds (u, phi) of the step being taken and pig
+    // the second moments sum_i c_ia c_ib g_i of the pulled g (6 planes in 3D,
+    // 3 in 2D).  P[cur], u[cur] are rebuilt from fa[cur] when read.
+    void *fa[2] = {nullptr, nullptr};
+    void *fb = nullptr;
+    void *pig = nullptr;
+    bool fa_valid = false;         // fa[cur] holds the state
+    bool soa_valid = true;         // P[cur], u[cur] hold the state
     bool inplace = false;          // one population store, AA streaming
     uint32_t *mask = nullptr;
     int *d_err = nullptr;
@@ -110,7 +117,8 @@ struct Ops {
     int (*probe)(lbm_ctx *c, const long long *d_sites, int n, double *d_h, double *d_g, double *d_P, double *d_u);
     size_t (*step_smem)();
     bool (*has_v2)();
-    int (*pack)(lbm_ctx *c);       // f4[cur] from u[cur] (no-op without packed words)
+    int (*pack)(lbm_ctx *c);       // fa[cur] from P[cur], u[cur] when stale (no-op without packed words)
+    int (*sync_soa)(lbm_ctx *c);   // P[cur], u[cur] from fa[cur] when stale (no-op without packed words)
     // batched persistent launch (lbm_batch_*)
     size_t (*batch_member_bytes)();
     long long (*batch_items)(const lbm_ctx *c);

@@ -163,8 +163,10 @@ struct SplitArgs {
     const R *P_old, *u_old;   // P^n, u^n [D][N]
     R *P_new, *u_new;         // P^{n+1}, u^{n+1} [D][N]
     R *phi;                   // phi^{n+1} [N]
-    const float4 *F_old;      // packed (u^n, -) per site, FP32 arithmetic only (else NULL)
-    float4 *F_new;            // packed (u^{n+1}, phi^{n+1})
+    const float4 *F_old;      // packed (u^n, P^n) per site, FP32 arithmetic only (else NULL)
+    float4 *F_new;            // packed (u^{n+1}, P^{n+1})
+    float4 *FB;               // packed (u^{n+1}, phi^{n+1})
+    float *PiG;               // sum_i c_ia c_ib g_i of the pulled g, [3 or 6][N]
     const uint32_t *mask;
     int *err;
     int nx, ny, nz;
@@ -172,15 +174,31 @@ struct SplitArgs {
     SiteConsts<R> k;
 };
 
-// Velocity of one site packed in a 16-byte word (z component 0 in 2D; the
-// fourth lane, phi, is only read from words the moments launch wrote): the
-// split kernels read a neighbour's velocity with one load.
+// (u, P) of one site packed in a 16-byte word (z component 0 in 2D): the
+// split kernels read a neighbour's velocity and pressure with one load.
 template <int D>
-__global__ void __launch_bounds__(256) pack_kernel(const float *__restrict__ u, float4 *__restrict__ F, long long N)
+__global__ void __launch_bounds__(256) pack_kernel(const float *__restrict__ P, const float *__restrict__ u,
+                                                   float4 *__restrict__ F, long long N)
 {
     const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= N) return;
-    F[x] = make_float4(u[x], u[N + x], D == 3 ? u[2 * N + x] : 0.f, 0.f);
+    F[x] = make_float4(u[x], u[N + x], D == 3 ? u[2 * N + x] : 0.f, P[x]);
+}
+
+// The planes P, u[D] of the fluid sites from the packed words (solid sites
+// hold no state and keep their values).
+template <int D>
+__global__ void __launch_bounds__(256) unpack_kernel(const float4 *__restrict__ F, const uint32_t *__restrict__ mask,
+                                                     float *__restrict__ P, float *__restrict__ u, long long N)
+{
+    const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= N) return;
+    if (mask && (mask[x] & kSolidBit)) return;
+    const float4 f = F[x];
+    P[x] = f.w;
+    u[x] = f.x;
+    u[N + x] = f.y;
+    if (D == 3) u[2 * N + x] = f.z;
 }
 
 // Site coordinates and wrapped neighbour offsets: site of x + s c with

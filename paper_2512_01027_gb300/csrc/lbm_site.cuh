@@ -321,11 +321,20 @@ __device__ __forceinline__ R s1_pressure(const SiteConsts<R> &k, const R *gp, co
 // so each pair needs one c.u and two dot products with per-site vectors.
 // The same formulas as the canonical collide below, regrouped; divisions by
 // per-site quantities become one reciprocal each.
-template <class L, bool INIT, bool PDEV>
+// GMOM: instead of the pulled g (gp), the filter gets its second moments
+// pig = sum_i c_ia c_ib g_i (xx, xy, xz, yy, yz, zz in 3D; xx, xy, yy in 2D):
+// Pi = pig - sum_i c_ia c_ib g_eq_i is all the filter needs of g.
+template <int D>
+__host__ __device__ constexpr int pig_slot(int a, int b)
+{
+    return D == 3 ? (a == 0 ? b : (a == 1 ? 2 + b : 5)) : (a == 0 ? b : 2);
+}
+
+template <class L, bool INIT, bool PDEV, bool GMOM = false>
 __device__ __forceinline__ void collide_pairs(const SiteConsts<float> &k, float phi, float phihat, float rho,
                                               float P, const float (&u)[3], const float (&gphi)[3], float lphi,
                                               const float (&gu)[3][3], const float *hp, const float *gp, float *hs,
-                                              float *gs)
+                                              float *gs, const float *pig = nullptr)
 {
     constexpr int D = L::D;
     constexpr int NP = (L::Q - 1) / 2;
@@ -432,7 +441,8 @@ __device__ __forceinline__ void collide_pairs(const SiteConsts<float> &k, float 
         } else {
             hs[i] = hp[i] - (hp[i] - (eh + oh)) * k.inv_tau_phi;
             hs[i + 1] = hp[i + 1] - (hp[i + 1] - (eh - oh)) * k.inv_tau_phi;
-            ne[p] = (gp[i] + gp[i + 1]) - 2.f * eg[p];   // (g - g_eq) summed over the pair
+            if constexpr (GMOM) ne[p] = -2.f * eg[p];      // - g_eq summed over the pair
+            else ne[p] = (gp[i] + gp[i + 1]) - 2.f * eg[p];   // (g - g_eq) summed over the pair
         }
     });
     if constexpr (!INIT) {
@@ -443,6 +453,7 @@ __device__ __forceinline__ void collide_pairs(const SiteConsts<float> &k, float 
             static_for<a, D>([&](auto Bb) {
                 constexpr int b = decltype(Bb)::value;
                 float acc = 0.f;
+                if constexpr (GMOM) acc = pig[pig_slot<D>(a, b)];
                 static_for<0, NP>([&](auto Pp) {
                     constexpr int p = decltype(Pp)::value;
                     constexpr int cc = L::c(2 * p + 1, a) * L::c(2 * p + 1, b);

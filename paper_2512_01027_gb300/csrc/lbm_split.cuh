@@ -98,9 +98,12 @@ __device__ __forceinline__ IX write_idx(IX N, const Nbr32 &nb, int idx, uint32_t
     }
 }
 
-// FP32 arithmetic also keeps (u, phi) of each site as one packed 16-byte
-// word: the moments launch reads a neighbour's velocity with one load, the
-// collision launch its velocity and phi.
+// FP32 arithmetic keeps the state (u, P) of each site as one packed 16-byte
+// word while it steps in the split form: the moments launch reads a
+// neighbour's velocity and pressure with one load.  It also leaves for the
+// collision launch the packed (u, phi) words of the new step and the second
+// moments sum_i c_ia c_ib g_i of the pulled g, which is all the filter
+// collision needs of g, so the collision launch pulls h only.
 template <class R>
 inline constexpr bool kPacked = std::is_same<R, float>::value;
 
@@ -118,7 +121,9 @@ __device__ __forceinline__ void moments_site(const SplitArgs<R, typename C::S> &
     const IX N = (IX)a.N;
     const Nbr32 nb(idx, a.nx, a.ny, D == 3 ? a.nz : 1);
     R hp[Q], gp[Q], Pn[Q], K[Q];
-    const R P0 = a.P_old[idx];
+    R P0;
+    if constexpr (kPacked<R>) P0 = a.F_old[idx].w;
+    else P0 = a.P_old[idx];
     R sum_wcu = R(0);
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
@@ -133,7 +138,7 @@ __device__ __forceinline__ void moments_site(const SplitArgs<R, typename C::S> &
             R un[3];
             if constexpr (kPacked<R>) {
                 const float4 f = a.F_old[src];
-                Pn[i] = bb ? P0 : a.P_old[src];
+                Pn[i] = bb ? P0 : f.w;
                 un[0] = f.x; un[1] = f.y; un[2] = f.z;
             } else {
                 Pn[i] = bb ? P0 : a.P_old[src];
@@ -158,13 +163,38 @@ __device__ __forceinline__ void moments_site(const SplitArgs<R, typename C::S> &
         s1_moments<L, R>(a.k, hp, gp, Pn, P0, phi, phihat, rho, u, K);
         Pnew = s1_pressure<L, R, C::kPdev>(a.k, gp, K, rho, sum_wcu, P0);
     }
-    a.P_new[idx] = Pnew;
-    static_for<0, D>([&](auto A) {
-        constexpr int ax = decltype(A)::value;
-        a.u_new[eidx<IX>(ax, N, idx)] = u[ax];
-    });
-    if constexpr (kPacked<R>) a.F_new[idx] = make_float4(u[0], u[1], D == 3 ? u[2] : 0.f, phi);
-    else a.phi[idx] = phi;
+    if constexpr (kPacked<R>) {
+        const float uz = D == 3 ? u[2] : 0.f;
+        a.F_new[idx] = make_float4(u[0], u[1], uz, Pnew);
+        a.FB[idx] = make_float4(u[0], u[1], uz, phi);
+        // sum_i c_ia c_ib g_i, per pair (c_ia c_ib is even in c)
+        constexpr int NS = D == 3 ? 6 : 3;
+        float pm[NS];
+        static_for<0, NS>([&](auto J) { pm[decltype(J)::value] = 0.f; });
+        static_for<0, (Q - 1) / 2>([&](auto Pp) {
+            constexpr int i = 2 * decltype(Pp)::value + 1;
+            const float gsum = gp[i] + gp[i + 1];
+            static_for<0, D>([&](auto A) {
+                constexpr int a0 = decltype(A)::value;
+                static_for<a0, D>([&](auto Bb) {
+                    constexpr int b0 = decltype(Bb)::value;
+                    constexpr int cc = L::c(i, a0) * L::c(i, b0);
+                    if constexpr (cc != 0) acc_c<cc>(pm[pig_slot<D>(a0, b0)], gsum);
+                });
+            });
+        });
+        static_for<0, NS>([&](auto J) {
+            constexpr int j = decltype(J)::value;
+            a.PiG[eidx<IX>(j, N, idx)] = pm[j];
+        });
+    } else {
+        a.P_new[idx] = Pnew;
+        static_for<0, D>([&](auto A) {
+            constexpr int ax = decltype(A)::value;
+            a.u_new[eidx<IX>(ax, N, idx)] = u[ax];
+        });
+        a.phi[idx] = phi;
+    }
 }
 
 // S0 + S2..S5 at site idx (0 <= idx < a.N).
@@ -180,15 +210,17 @@ __device__ __forceinline__ void collide_site(const SplitArgs<R, typename C::S> &
     // S2: stencils of phi^{n+1} and u^{n+1} from the fields of the moments launch
     R phi, gphi[3], lphi;
     R u[3], gu[3][3];
-    const R P = a.P_new[idx];
+    R P;
     if constexpr (kPacked<R>) {
-        const float4 f0 = a.F_new[idx];
+        const float4 f0 = a.FB[idx];
         u[0] = f0.x; u[1] = f0.y; u[2] = f0.z;
         phi = f0.w;
-        auto at = [&](auto I, int s) { return a.F_new[nb.at<L, decltype(I)::value>(s)]; };
+        P = a.F_new[idx].w;
+        auto at = [&](auto I, int s) { return a.FB[nb.at<L, decltype(I)::value>(s)]; };
         if (m == 0u) stencil_packed<L, false>(at, m, phi, gphi, lphi, gu);
         else stencil_packed<L, true>(at, m, phi, gphi, lphi, gu);
     } else {
+        P = a.P_new[idx];
         phi = a.phi[idx];
         stencil_any<L, R>([&](auto I, int s) { return a.phi[nb.at<L, decltype(I)::value>(s)]; }, m, phi, phi, gphi,
                           lphi);
@@ -205,14 +237,30 @@ __device__ __forceinline__ void collide_site(const SplitArgs<R, typename C::S> &
     }
     const R phihat = a.k.clamp ? clamp01(phi) : phi;
     const R rho = a.k.rho_a + phihat * a.k.drho;
-    R hp[Q], gp[Q], hs[Q], gs[Q];
-    static_for<0, Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        const IX e = read_idx<L, MODE, i, IX>(N, nb, idx, m, HAS_MASK);
-        hp[i] = C::template dec_h<i>(a.src_h[e]);
-        gp[i] = C::template dec_g<i>(a.src_g[e]);
-    });
-    collide<L, R, false, C::kPdev>(a.k, phi, phihat, rho, P, u, gphi, lphi, gu, hp, gp, hs, gs);
+    R hp[Q], hs[Q], gs[Q];
+    if constexpr (kPacked<R>) {
+        static_for<0, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            hp[i] = C::template dec_h<i>(a.src_h[read_idx<L, MODE, i, IX>(N, nb, idx, m, HAS_MASK)]);
+        });
+        constexpr int NS = D == 3 ? 6 : 3;
+        float pm[NS];
+        static_for<0, NS>([&](auto J) {
+            constexpr int j = decltype(J)::value;
+            pm[j] = a.PiG[eidx<IX>(j, N, idx)];
+        });
+        collide_pairs<L, false, C::kPdev, true>(a.k, phi, phihat, rho, P, u, gphi, lphi, gu, hp, nullptr, hs, gs,
+                                               pm);
+    } else {
+        R gp[Q];
+        static_for<0, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            const IX e = read_idx<L, MODE, i, IX>(N, nb, idx, m, HAS_MASK);
+            hp[i] = C::template dec_h<i>(a.src_h[e]);
+            gp[i] = C::template dec_g<i>(a.src_g[e]);
+        });
+        collide<L, R, false, C::kPdev>(a.k, phi, phihat, rho, P, u, gphi, lphi, gu, hp, gp, hs, gs);
+    }
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         const IX e = write_idx<L, MODE, i, IX>(N, nb, idx, m, HAS_MASK);

@@ -108,11 +108,12 @@ def test_no_cpu_fallback_without_a_device():
 
 def test_footprint_estimate_needs_no_device():
     """Admission control sizes a lattice before creating it: populations
-    (2 sets in place, 4 ping-pong), P, u (two each), phi, packed (u, phi)
-    words (two, FP32 arithmetic only), scratch, mask."""
+    (2 sets in place, 4 ping-pong), P, u (two each), phi; with FP32
+    arithmetic the packed (u, P) words (two), the packed (u, phi) words and
+    the six second moments of g; scratch, mask."""
     N = 32 ** 3
     scratch = 8 * (1024 * 8 + 64) + 256
-    packed = 2 * 16 * N
+    packed = (2 * 16 + 16 + 4 * 6) * N
     got = lbm.estimate_footprint("D3Q27", (32, 32, 32), storage="f16", inplace=1)
     assert got == 2 * 27 * N * 2 + 9 * N * 4 + packed + scratch
     got = lbm.estimate_footprint("D3Q27", (32, 32, 32), periodic=(1, 1, 0), storage="f32")
