@@ -52,6 +52,7 @@ extern "C" {
 #define LBM_ERR_CUDA 3          /* a CUDA runtime call or kernel launch failed */
 #define LBM_ERR_NONFINITE 4     /* a step produced a non-finite phi, P or u */
 #define LBM_ERR_UNSUPPORTED 5   /* valid request this build does not implement */
+#define LBM_ERR_TIMEOUT 6       /* a bounded wait inside a kernel ran out; the step's results are invalid */
 
 typedef struct lbm_ctx *lbm_handle;
 
@@ -189,8 +190,12 @@ int lbm_load_state(lbm_handle h, const void *host_buf, size_t bytes);
  * automatic (the split form), 1 = fused plane-synchronous kernel, 2 = fused
  * pipelined kernel (3D lattices with 4-byte populations, else
  * LBM_ERR_UNSUPPORTED), 3 = split form (two launches per step: moments, then
- * stencils + collisions).  An in-place handle always uses the split form
- * (variants 1 and 2 are LBM_ERR_UNSUPPORTED there).  zchunk: z planes per
+ * stencils + collisions), 4 = persistent split form (both phases in one
+ * launch per step: blocks take plane-ordered work items so that the
+ * collision of a plane follows the moments of the next one while their data
+ * is in L2; FP32 arithmetic and Q x sites < 2^32, else LBM_ERR_UNSUPPORTED).
+ * An in-place handle always uses a split form (variants 1 and 2 are
+ * LBM_ERR_UNSUPPORTED there).  zchunk: z planes per
  * block of the fused kernels (0 = automatic); it never changes results.
  * Every variant evaluates the same formulas in the same order: with FP64
  * storage (built without FMA contraction) all variants agree bit for bit;
@@ -240,14 +245,15 @@ const char *lbm_last_error(lbm_handle h);
 
 /* ------------------------------------------------------------------------
  * Autotuner.  Times `trial_steps` steps of every launch form the handle
- * supports (split form; fused plane-synchronous kernel; fused pipelined
- * kernel at several z-chunks where available) on the handle's own state,
+ * supports (split form; persistent split form; fused plane-synchronous
+ * kernel; fused pipelined kernel at several z-chunks, where available) on
+ * the handle's own state,
  * keeps the fastest with lbm_set_tuning and restores the state it started
  * from (through a host copy of lbm_state_bytes bytes), so the results of the
  * following steps are those of the chosen variant from the same state.
  * Outputs (any may be NULL): the chosen variant and zchunk and its measured
- * milliseconds per step.  An in-place handle has one form and returns it
- * without timing.  Synchronises; 1 <= trial_steps <= 1000. */
+ * milliseconds per step.  An in-place handle tries the split forms only.
+ * Synchronises; 1 <= trial_steps <= 1000. */
 int lbm_autotune(lbm_handle h, int trial_steps, int *variant, int *zchunk, double *ms_per_step);
 
 /* ------------------------------------------------------------------------

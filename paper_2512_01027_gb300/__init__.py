@@ -28,8 +28,9 @@ F64, F32, F16DEV, BF16DEV = 0, 1, 2, 3
 LATTICES = {"D2Q9": D2Q9, "D3Q19": D3Q19, "D3Q27": D3Q27}
 STORAGES = {"f64": F64, "f32": F32, "f16": F16DEV, "bf16": BF16DEV}
 
-LBM_OK, LBM_ERR_INVALID_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_NONFINITE, LBM_ERR_UNSUPPORTED = range(6)
-_ERR_NAMES = {1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NONFINITE", 5: "UNSUPPORTED"}
+(LBM_OK, LBM_ERR_INVALID_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_NONFINITE, LBM_ERR_UNSUPPORTED,
+ LBM_ERR_TIMEOUT) = range(7)
+_ERR_NAMES = {1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "NONFINITE", 5: "UNSUPPORTED", 6: "TIMEOUT"}
 
 
 class LbmError(RuntimeError):
@@ -356,8 +357,8 @@ class Lattice:
         _check(lib().lbm_load_state(self._h, buf, len(data)), self._h)
 
     def set_tuning(self, variant: int = 0, zchunk: int = 0):
-        """variant 0 auto, 1 fused plane-synchronous, 2 fused pipelined, 3 split form;
-        zchunk 0 = auto."""
+        """variant 0 auto, 1 fused plane-synchronous, 2 fused pipelined, 3 split form,
+        4 persistent split form; zchunk 0 = auto."""
         _check(lib().lbm_set_tuning(self._h, int(variant), int(zchunk)), self._h)
 
     def autotune(self, trial_steps: int = 5):

@@ -129,13 +129,13 @@ size_t compute_bytes(int storage) { return storage == LBM_STORE_F64 ? 8 : 4; }
 
 // Device bytes of a handle: population sets, P and u (two each), phi,
 // reduction scratch, error flag, and the neighbour mask when there is one.
-size_t footprint_bytes(int Q, int D, long long N, int storage, bool inplace, bool has_mask)
+size_t footprint_bytes(int Q, int D, long long N, int nz, int storage, bool inplace, bool has_mask)
 {
     const size_t pop = (size_t)Q * (size_t)N * storage_bytes(storage);
     const size_t field = (size_t)N * compute_bytes(storage);
     size_t s = (inplace ? 2 : 4) * pop + (3 + 2 * (size_t)D) * field + sizeof(double) * kScratchDoubles + 256;
     // FP32 arithmetic: packed (u, P) ping-pong, packed (u, phi), second moments of g
-    if (storage != LBM_STORE_F64) s += (2 * 16 + 16 + 4 * (D == 3 ? 6 : 3)) * (size_t)N;
+    if (storage != LBM_STORE_F64) s += (2 * 16 + 16 + 4 * (D == 3 ? 6 : 3)) * (size_t)N + 4 * (2 + (size_t)nz);
     if (has_mask) s += sizeof(uint32_t) * (size_t)N;
     return s;
 }
@@ -162,6 +162,7 @@ int sync_and_check(lbm_ctx *c)
     int flag = 0;
     e = cudaMemcpy(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy(err flag)");
+    if (flag & 2) return fail(c, LBM_ERR_TIMEOUT, "a wait of the persistent step ran out (results invalid)");
     if (flag) return fail(c, LBM_ERR_NONFINITE, "a step produced a non-finite phi, P or u");
     return LBM_OK;
 }
@@ -329,7 +330,8 @@ int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params, lbm_
         c->fa[1] = own(c, 16 * (size_t)N);
         c->fb = own(c, 16 * (size_t)N);
         c->pig = own(c, 4 * (size_t)(D == 3 ? 6 : 3) * (size_t)N);
-        if (!c->fa[0] || !c->fa[1] || !c->fb || !c->pig) c->phi = nullptr;
+        c->pctl = static_cast<int *>(own(c, sizeof(int) * (2 + (size_t)c->nz)));
+        if (!c->fa[0] || !c->fa[1] || !c->fb || !c->pig || !c->pctl) c->phi = nullptr;
     }
     if (!c->phi) {
         g_create_err = "device allocation of the phi field or the packed words failed";
@@ -618,7 +620,9 @@ int lbm_load_state(lbm_handle h, const void *host_buf, size_t bytes)
 int lbm_set_tuning(lbm_handle h, int variant, int zchunk)
 {
     if (!h) return LBM_ERR_INVALID_ARG;
-    if (variant < 0 || variant > 3 || zchunk < 0) return fail(h, LBM_ERR_INVALID_ARG, "variant in 0..3, zchunk >= 0");
+    if (variant < 0 || variant > 4 || zchunk < 0) return fail(h, LBM_ERR_INVALID_ARG, "variant in 0..4, zchunk >= 0");
+    if (variant == 4 && !h->ops->persist_ok(h))
+        return fail(h, LBM_ERR_UNSUPPORTED, "the persistent step needs FP32 arithmetic and Q * sites < 2^32");
     if (variant == 2 && !h->ops->has_v2())
         return fail(h, LBM_ERR_UNSUPPORTED, "pipelined kernel needs a 3D lattice with FP32 populations");
     if (h->inplace && (variant == 1 || variant == 2))
@@ -631,7 +635,7 @@ int lbm_set_tuning(lbm_handle h, int variant, int zchunk)
 int lbm_footprint(lbm_handle h, size_t *device_bytes, size_t *step_bytes)
 {
     if (!h) return LBM_ERR_INVALID_ARG;
-    if (device_bytes) *device_bytes = footprint_bytes(h->Q, h->D, h->N, h->storage, h->inplace, h->mask != nullptr);
+    if (device_bytes) *device_bytes = footprint_bytes(h->Q, h->D, h->N, h->nz, h->storage, h->inplace, h->mask != nullptr);
     if (step_bytes) *step_bytes = 2 * (2 * h->pop_bytes) + 2 * (size_t)(1 + h->D) * h->field_bytes;
     return LBM_OK;
 }
@@ -647,7 +651,7 @@ int lbm_estimate_footprint(const lbm_grid *grid, int lattice, const lbm_params *
     bool mask = !grid->periodic[0] || !grid->periodic[1] || (D == 3 && !grid->periodic[2]);
     if (grid->solid)
         for (long long i = 0; i < N && !mask; ++i) mask = grid->solid[i] != 0;
-    *device_bytes = footprint_bytes(Q, D, N, params->storage, params->inplace == 1, mask);
+    *device_bytes = footprint_bytes(Q, D, N, grid->nz, params->storage, params->inplace == 1, mask);
     return LBM_OK;
 }
 

@@ -311,6 +311,7 @@ int lbm_autotune(lbm_handle h, int trial_steps, int *variant, int *zchunk, doubl
     };
     std::vector<Cand> cands;
     cands.push_back({3, 0});
+    if (h->ops->persist_ok(h)) cands.push_back({4, 0});
     if (!h->inplace) {
         cands.push_back({1, 0});
         if (h->ops->has_v2() && h->D == 3)
@@ -319,8 +320,8 @@ int lbm_autotune(lbm_handle h, int trial_steps, int *variant, int *zchunk, doubl
     }
     const int v0 = h->variant, z0 = h->zchunk;
     if (cands.size() == 1) {
-        h->variant = 3;
-        if (variant) *variant = 3;
+        h->variant = cands[0].variant;
+        if (variant) *variant = cands[0].variant;
         if (zchunk) *zchunk = 0;
         if (ms_per_step) *ms_per_step = 0.0;
         return LBM_OK;

@@ -10,6 +10,7 @@
 #include "lbm_step_v2.cuh"
 #include "lbm_split.cuh"
 #include "lbm_batch.cuh"
+#include "lbm_persist.cuh"
 
 #include <type_traits>
 
@@ -236,9 +237,75 @@ struct Impl {
         return cudaGetLastError();
     }
 
+    // --- persistent split step (one launch per step) ------------------------
+    static bool persist_ok(const lbm_ctx *c)
+    {
+        return kPacked<R> && c->pctl != nullptr && split_idx32(L::Q, c->N);
+    }
+
+    template <bool M, int MODE>
+    static int launch_persist(lbm_ctx *c, const SplitArgs<R, S> &a)
+    {
+        if constexpr (kPacked<R>) {
+            static int grid = 0;
+            if (grid == 0) {
+                int sms = 0, per_sm = 0;
+                cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, split_persistent_kernel<L, C, M, MODE>,
+                                                              kSplitThreads, 0);
+                grid = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+            }
+            PersistArgs p;
+            p.ctl = c->pctl;
+            p.nz = L::D == 3 ? c->nz : 1;
+            p.nxy = (int)(c->N / p.nz);
+            p.bpp = (p.nxy + kSplitThreads - 1) / kSplitThreads;
+            p.zper = L::D == 3 ? c->periodic[2] : 1;
+            p.lag = kPersistLag;
+            p.err = c->d_err;
+            const long long items = 2LL * p.nz * p.bpp;
+            const int g = (int)std::min<long long>(grid, items);
+            int rc = cuda_fail(c, cudaMemsetAsync(c->pctl, 0, sizeof(int) * (2 + (size_t)p.nz), c->stream),
+                               "cudaMemsetAsync(persistent counters)");
+            if (rc != LBM_OK) return rc;
+            split_persistent_kernel<L, C, M, MODE><<<g, kSplitThreads, 0, c->stream>>>(a, p);
+            return cuda_fail(c, cudaGetLastError(), "split_persistent_kernel launch");
+        } else {
+            return LBM_ERR_UNSUPPORTED;
+        }
+    }
+
+    static int step_persist(lbm_ctx *c, int64_t n)
+    {
+        if (n > 0) {
+            const int rc = pack(c);
+            if (rc != LBM_OK) return rc;
+        }
+        for (int64_t s = 0; s < n; ++s) {
+            const SplitArgs<R, S> a = split_args(c, 0);
+            const int mode = split_mode(c, c->steps);
+            int rc;
+            if (c->has_mask) {
+                if (mode == kPingPong) rc = launch_persist<true, kPingPong>(c, a);
+                else if (mode == kAAOdd) rc = launch_persist<true, kAAOdd>(c, a);
+                else rc = launch_persist<true, kAAEven>(c, a);
+            } else {
+                if (mode == kPingPong) rc = launch_persist<false, kPingPong>(c, a);
+                else if (mode == kAAOdd) rc = launch_persist<false, kAAOdd>(c, a);
+                else rc = launch_persist<false, kAAEven>(c, a);
+            }
+            if (rc != LBM_OK) return rc;
+            c->cur = 1 - c->cur;
+            c->steps += 1;
+            c->soa_valid = false;
+        }
+        return LBM_OK;
+    }
+
     static int step(lbm_ctx *c, int64_t n)
     {
-        if (c->inplace || c->variant == 3 || c->variant == 0) return step_split(c, n);
+        if (c->variant == 4 && persist_ok(c)) return step_persist(c, n);
+        if (c->inplace || c->variant == 3 || c->variant == 0 || c->variant == 4) return step_split(c, n);
         if (n > 0) {
             const int rc = sync_soa(c);
             if (rc != LBM_OK) return rc;
@@ -369,7 +436,7 @@ struct Impl {
     {
         static const Ops o = {&init,      &step,       &read,         &reduce,      &pjump,
                               &probe,     &step_smem,  &has_v2,       &pack,        &sync_soa,
-                              &batch_member_bytes,
+                              &persist_ok, &batch_member_bytes,
                               &batch_items, &batch_fill, &batch_grid, &batch_launch};
         return &o;
     }

@@ -64,6 +64,7 @@ struct lbm_ctx {
     void *fa[2] = {nullptr, nullptr};
     void *fb = nullptr;
     void *pig = nullptr;
+    int *pctl = nullptr;           // counters of the persistent split step [2 + nz]
     bool fa_valid = false;         // fa[cur] holds the state
     bool soa_valid = true;         // P[cur], u[cur] hold the state
     bool inplace = false;          // one population store, AA streaming
@@ -119,6 +120,7 @@ struct Ops {
     bool (*has_v2)();
     int (*pack)(lbm_ctx *c);       // fa[cur] from P[cur], u[cur] when stale (no-op without packed words)
     int (*sync_soa)(lbm_ctx *c);   // P[cur], u[cur] from fa[cur] when stale (no-op without packed words)
+    bool (*persist_ok)(const lbm_ctx *c);   // the persistent split step is available
     // batched persistent launch (lbm_batch_*)
     size_t (*batch_member_bytes)();
     long long (*batch_items)(const lbm_ctx *c);

@@ -197,8 +197,17 @@ __device__ __forceinline__ void moments_site(const SplitArgs<R, typename C::S> &
     }
 }
 
+// Load that bypasses L1 when CG: for data other blocks wrote earlier in the
+// same launch (the persistent step).
+template <bool CG, class T>
+__device__ __forceinline__ T ld_maybe_cg(const T *p)
+{
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
 // S0 + S2..S5 at site idx (0 <= idx < a.N).
-template <class L, class R, class C, bool HAS_MASK, int MODE, class IX>
+template <class L, class R, class C, bool HAS_MASK, int MODE, class IX, bool CG = false>
 __device__ __forceinline__ void collide_site(const SplitArgs<R, typename C::S> &a, const int idx)
 {
     constexpr int D = L::D, Q = L::Q;
@@ -212,11 +221,11 @@ __device__ __forceinline__ void collide_site(const SplitArgs<R, typename C::S> &
     R u[3], gu[3][3];
     R P;
     if constexpr (kPacked<R>) {
-        const float4 f0 = a.FB[idx];
+        const float4 f0 = ld_maybe_cg<CG>(a.FB + idx);
         u[0] = f0.x; u[1] = f0.y; u[2] = f0.z;
         phi = f0.w;
-        P = a.F_new[idx].w;
-        auto at = [&](auto I, int s) { return a.FB[nb.at<L, decltype(I)::value>(s)]; };
+        P = ld_maybe_cg<CG>(a.F_new + idx).w;
+        auto at = [&](auto I, int s) { return ld_maybe_cg<CG>(a.FB + nb.at<L, decltype(I)::value>(s)); };
         if (m == 0u) stencil_packed<L, false>(at, m, phi, gphi, lphi, gu);
         else stencil_packed<L, true>(at, m, phi, gphi, lphi, gu);
     } else {
@@ -247,7 +256,7 @@ __device__ __forceinline__ void collide_site(const SplitArgs<R, typename C::S> &
         float pm[NS];
         static_for<0, NS>([&](auto J) {
             constexpr int j = decltype(J)::value;
-            pm[j] = a.PiG[eidx<IX>(j, N, idx)];
+            pm[j] = ld_maybe_cg<CG>(a.PiG + eidx<IX>(j, N, idx));
         });
         collide_pairs<L, false, C::kPdev, true>(a.k, phi, phihat, rho, P, u, gphi, lphi, gu, hp, nullptr, hs, gs,
                                                pm);

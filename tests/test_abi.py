@@ -113,7 +113,7 @@ def test_footprint_estimate_needs_no_device():
     the six second moments of g; scratch, mask."""
     N = 32 ** 3
     scratch = 8 * (1024 * 8 + 64) + 256
-    packed = (2 * 16 + 16 + 4 * 6) * N
+    packed = (2 * 16 + 16 + 4 * 6) * N + 4 * (2 + 32)
     got = lbm.estimate_footprint("D3Q27", (32, 32, 32), storage="f16", inplace=1)
     assert got == 2 * 27 * N * 2 + 9 * N * 4 + packed + scratch
     got = lbm.estimate_footprint("D3Q27", (32, 32, 32), periodic=(1, 1, 0), storage="f32")

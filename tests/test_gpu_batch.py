@@ -143,7 +143,7 @@ def test_autotune_keeps_state(lbm):
     L = make(lbm, c, "f32")
     L.step(3)
     v, z, ms = L.autotune(3)
-    assert v in (1, 2, 3) and ms > 0
+    assert v in (1, 2, 3, 4) and ms > 0
     assert L.steps_done == 3
     L.step(5)
     R = make(lbm, c, "f32")
@@ -152,6 +152,6 @@ def test_autotune_keeps_state(lbm):
     R.step(5)
     for x, y in zip(R.read_fields(), L.read_fields()):
         assert np.array_equal(x, y)
-    # an in-place store has one form
+    # an in-place store has the split forms only
     I = make(lbm, c, "f32", inplace=1)
-    assert I.autotune(2)[0] == 3
+    assert I.autotune(2)[0] in (3, 4)

@@ -156,3 +156,41 @@ def test_inplace_refuses_fused_variants(lbm):
         with pytest.raises(lbm.LbmError) as e:
             L.set_tuning(v, 0)
         assert e.value.code == lbm.LBM_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("inplace", [0, 1])
+@pytest.mark.parametrize("case", ["closed_box_d3q27", "periodic_thin_d3q27", "walls_d3q19", "droplet_2d",
+                                  "closed_box_2d"])
+def test_persistent_matches_split(lbm, case, storage, inplace):
+    """The persistent split step (one launch per step, plane-ordered work
+    items with waits) runs the split form's per-site code: it must agree with
+    the two-launch form to rounding (the compiler may contract differently in
+    another kernel), after odd and even step counts, with walls, random
+    solids, z-periodic wrap and 2D lattices."""
+    c = CASES[case]()
+    for steps in (9, 14):
+        a = make(lbm, c, storage, variant=3, inplace=inplace)
+        b = make(lbm, c, storage, variant=4, inplace=inplace)
+        a.step(steps)
+        b.step(steps)
+        b.check()
+        fa, fb = a.read_fields(), b.read_fields()
+        for x, y in zip(fa, fb):
+            assert np.all(np.isfinite(y))
+        if storage == "f32":
+            for x, y in zip(fa, fb):
+                assert np.abs(x - y).max() <= 1e-6 * max(np.abs(x).max(), 1e-30)
+        else:
+            # a rounding difference can move a 16-bit code by one step
+            assert np.abs(fa[0] - fb[0]).max() <= 2 * steps * 2.0 ** -12
+            for x, y in zip(fa[1:], fb[1:]):
+                assert np.abs(x - y).max() <= 1e-2 * max(np.abs(x).max(), 1e-30)
+
+
+def test_persistent_refused_for_f64(lbm):
+    c = CASES["walls_d3q19"]()
+    L = make(lbm, c, "f64")
+    with pytest.raises(lbm.LbmError) as e:
+        L.set_tuning(4, 0)
+    assert e.value.code == lbm.LBM_ERR_UNSUPPORTED
