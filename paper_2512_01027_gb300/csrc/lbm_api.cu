@@ -136,6 +136,8 @@ size_t footprint_bytes(int Q, int D, long long N, int nz, int storage, bool inpl
     size_t s = (inplace ? 2 : 4) * pop + (3 + 2 * (size_t)D) * field + sizeof(double) * kScratchDoubles + 256;
     // FP32 arithmetic: packed (u, P) ping-pong, packed (u, phi), second moments of g
     if (storage != LBM_STORE_F64) s += (2 * 16 + 16 + 4 * (D == 3 ? 6 : 3)) * (size_t)N + 4 * (2 + (size_t)nz);
+    // BF16 storage: odd part of g per site, ping-pong
+    if (storage == LBM_STORE_BF16DEV) s += 2 * 16 * (size_t)N;
     if (has_mask) s += sizeof(uint32_t) * (size_t)N;
     return s;
 }
@@ -331,6 +333,11 @@ int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params, lbm_
         c->fb = own(c, 16 * (size_t)N);
         c->pig = own(c, 4 * (size_t)(D == 3 ? 6 : 3) * (size_t)N);
         c->pctl = static_cast<int *>(own(c, sizeof(int) * (2 + (size_t)c->nz)));
+        if (storage == LBM_STORE_BF16DEV) {
+            c->fg[0] = own(c, 16 * (size_t)N);
+            c->fg[1] = own(c, 16 * (size_t)N);
+            if (!c->fg[0] || !c->fg[1]) c->phi = nullptr;
+        }
         if (!c->fa[0] || !c->fa[1] || !c->fb || !c->pig || !c->pctl) c->phi = nullptr;
     }
     if (!c->phi) {
@@ -575,6 +582,7 @@ int lbm_save_state(lbm_handle h, void *host_buf, size_t bytes)
     std::memcpy(p, &hd, sizeof hd);
     p += sizeof hd;
     if (const int rs = h->ops->sync_soa(h); rs != LBM_OK) return rs;
+    if (const int rf = h->ops->fold(h); rf != LBM_OK) return rf;
     const int b = h->cur;
     int rc = cuda_fail(h, cudaMemcpyAsync(p, h->h[b], h->pop_bytes, cudaMemcpyDeviceToHost, h->stream), "D2H state");
     p += h->pop_bytes;
@@ -614,6 +622,7 @@ int lbm_load_state(lbm_handle h, const void *host_buf, size_t bytes)
     if (rc == LBM_OK) std::memcpy(&h->steps, p, sizeof(int64_t));
     h->fa_valid = false;
     h->soa_valid = true;
+    h->g_deferred = false;
     return rc;
 }
 

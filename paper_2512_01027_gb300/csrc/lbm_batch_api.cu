@@ -211,11 +211,13 @@ int lbm_batch_step(lbm_batch b, int64_t n, int *finished)
             if (take[j] > 0) order.push_back((int)j);
         }
         if (order.empty()) break;
-        // packed state words of members whose state was (re)loaded or fused-stepped
+        // packed state words (and, with BF16 storage, the deferred odd part
+        // of g) of members whose state was (re)loaded or fused-stepped
         for (int j : order) {
             lbm_ctx *h = b->members[j];
-            if (h->fa_valid) continue;
-            rc = b->ops->pack(h);
+            const bool godd = h->storage == LBM_STORE_BF16DEV;
+            if (h->fa_valid && (h->g_deferred || !godd)) continue;
+            rc = b->ops->split_prepare(h);
             if (rc == LBM_OK) rc = bcuda(b, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize(member)");
             if (rc != LBM_OK) {
                 b->err = "packing a member's state failed: " + h->err;
@@ -258,6 +260,7 @@ int lbm_batch_step(lbm_batch b, int64_t n, int *finished)
             h->steps += take[j];
             if (take[j] & 1) h->cur = 1 - h->cur;
             if (h->storage != LBM_STORE_F64) h->soa_valid = false;   // the state is in fa[cur]
+            if (h->storage == LBM_STORE_BF16DEV) h->g_deferred = true;
             b->remaining[j] -= take[j];
         }
         n -= K;

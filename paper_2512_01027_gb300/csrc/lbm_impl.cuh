@@ -120,6 +120,8 @@ struct Impl {
         a.F_new = static_cast<float4 *>(c->fa[dst]);
         a.FB = static_cast<float4 *>(c->fb);
         a.PiG = static_cast<float *>(c->pig);
+        a.G_old = static_cast<const float4 *>(c->fg[src]);
+        a.G_new = static_cast<float4 *>(c->fg[dst]);
         a.src_h = static_cast<const S *>(c->h[src]);
         a.src_g = static_cast<const S *>(c->g[src]);
         a.dst_h = static_cast<S *>(c->h[dst]);
@@ -155,6 +157,35 @@ struct Impl {
         }
     }
 
+    // Before split steps: packed (u, P) words; with BF16 storage V_g = 0
+    // when the store holds complete g* (the first pull adds nothing).
+    static int split_prepare(lbm_ctx *c)
+    {
+        int rc = pack(c);
+        if constexpr (kPacked<R> && C::kGodd) {
+            if (rc == LBM_OK && !c->g_deferred && c->fg[c->cur])
+                rc = cuda_fail(c, cudaMemsetAsync(c->fg[c->cur], 0, 16 * (size_t)c->N, c->stream),
+                               "cudaMemsetAsync(V_g)");
+        }
+        return rc;
+    }
+
+    // Complete g* in the store (BF16 storage, odd part deferred).
+    static int fold(lbm_ctx *c)
+    {
+        if constexpr (kPacked<R> && C::kGodd) {
+            if (!c->g_deferred) return LBM_OK;
+            const unsigned blocks = (unsigned)((c->N + 127) / 128);
+            fold_g_kernel<L, C><<<blocks, 128, 0, c->stream>>>(read_args(c), static_cast<S *>(c->g[c->cur]),
+                                                              static_cast<const float4 *>(c->fg[c->cur]));
+            const int rc = cuda_fail(c, cudaGetLastError(), "fold_g_kernel launch");
+            if (rc == LBM_OK) c->g_deferred = false;
+            return rc;
+        } else {
+            return LBM_OK;
+        }
+    }
+
     // The planes P[cur], u[cur] from the packed words, when they are stale.
     static int sync_soa(lbm_ctx *c)
     {
@@ -175,7 +206,7 @@ struct Impl {
     static int step_split(lbm_ctx *c, int64_t n)
     {
         if (n > 0) {
-            const int rc = pack(c);
+            const int rc = split_prepare(c);
             if (rc != LBM_OK) return rc;
         }
         for (int64_t s = 0; s < n; ++s) {
@@ -188,7 +219,10 @@ struct Impl {
             if (rc != LBM_OK) return rc;
             c->cur = 1 - c->cur;
             c->steps += 1;
-            if constexpr (kPacked<R>) c->soa_valid = false;   // the state is in fa[cur]
+            if constexpr (kPacked<R>) {
+                c->soa_valid = false;                      // the state is in fa[cur]
+                if constexpr (C::kGodd) c->g_deferred = true;   // fg[cur] holds V_g
+            }
         }
         return LBM_OK;
     }
@@ -278,7 +312,7 @@ struct Impl {
     static int step_persist(lbm_ctx *c, int64_t n)
     {
         if (n > 0) {
-            const int rc = pack(c);
+            const int rc = split_prepare(c);
             if (rc != LBM_OK) return rc;
         }
         for (int64_t s = 0; s < n; ++s) {
@@ -298,6 +332,7 @@ struct Impl {
             c->cur = 1 - c->cur;
             c->steps += 1;
             c->soa_valid = false;
+            if constexpr (C::kGodd) c->g_deferred = true;
         }
         return LBM_OK;
     }
@@ -307,7 +342,8 @@ struct Impl {
         if (c->variant == 4 && persist_ok(c)) return step_persist(c, n);
         if (c->inplace || c->variant == 3 || c->variant == 0 || c->variant == 4) return step_split(c, n);
         if (n > 0) {
-            const int rc = sync_soa(c);
+            int rc = sync_soa(c);
+            if (rc == LBM_OK) rc = fold(c);
             if (rc != LBM_OK) return rc;
         }
         StepArgs<R, S> a;
@@ -360,6 +396,7 @@ struct Impl {
         c->steps = 0;
         c->fa_valid = false;
         c->soa_valid = true;
+        c->g_deferred = false;
         return cuda_fail(c, cudaGetLastError(), "init_kernel launch");
     }
 
@@ -382,6 +419,8 @@ struct Impl {
     static int read(lbm_ctx *c, double *d_phi, double *d_P, double *d_u, double *d_hpop, double *d_gpop)
     {
         if (const int rs = sync_soa(c); rs != LBM_OK) return rs;
+        if (d_gpop)   // individual g*: complete the deferred odd part
+            if (const int rf = fold(c); rf != LBM_OK) return rf;
         ReadArgs<R, S> a = read_args(c);
         a.phi_out = d_phi; a.P_out = d_P; a.u_out = d_u; a.hpop_out = d_hpop; a.gpop_out = d_gpop;
         const int threads = 256;
@@ -426,6 +465,8 @@ struct Impl {
     static int probe(lbm_ctx *c, const long long *d_sites, int n, double *d_h, double *d_g, double *d_P, double *d_u)
     {
         if (const int rs = sync_soa(c); rs != LBM_OK) return rs;
+        if (d_g)
+            if (const int rf = fold(c); rf != LBM_OK) return rf;
         ReadArgs<R, S> a = read_args(c);
         const int threads = 128;
         probe_kernel<L, R, C><<<(n + threads - 1) / threads, threads, 0, c->stream>>>(a, d_sites, n, d_h, d_g, d_P, d_u);
@@ -436,7 +477,7 @@ struct Impl {
     {
         static const Ops o = {&init,      &step,       &read,         &reduce,      &pjump,
                               &probe,     &step_smem,  &has_v2,       &pack,        &sync_soa,
-                              &persist_ok, &batch_member_bytes,
+                              &persist_ok, &split_prepare, &fold, &batch_member_bytes,
                               &batch_items, &batch_fill, &batch_grid, &batch_launch};
         return &o;
     }

@@ -65,6 +65,8 @@ struct lbm_ctx {
     void *fb = nullptr;
     void *pig = nullptr;
     int *pctl = nullptr;           // counters of the persistent split step [2 + nz]
+    void *fg[2] = {nullptr, nullptr};   // BF16 storage: odd part V_g of g* per site (float4), follows cur
+    bool g_deferred = false;       // the g store holds g* without its odd part, fg[cur] holds V_g
     bool fa_valid = false;         // fa[cur] holds the state
     bool soa_valid = true;         // P[cur], u[cur] hold the state
     bool inplace = false;          // one population store, AA streaming
@@ -121,6 +123,8 @@ struct Ops {
     int (*pack)(lbm_ctx *c);       // fa[cur] from P[cur], u[cur] when stale (no-op without packed words)
     int (*sync_soa)(lbm_ctx *c);   // P[cur], u[cur] from fa[cur] when stale (no-op without packed words)
     bool (*persist_ok)(const lbm_ctx *c);   // the persistent split step is available
+    int (*split_prepare)(lbm_ctx *c);       // packed words and deferred-g state before split steps
+    int (*fold)(lbm_ctx *c);                // g* complete in the store again (BF16 storage)
     // batched persistent launch (lbm_batch_*)
     size_t (*batch_member_bytes)();
     long long (*batch_items)(const lbm_ctx *c);

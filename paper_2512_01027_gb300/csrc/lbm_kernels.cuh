@@ -40,6 +40,7 @@ template <class R, bool PD>
 struct CodecId {
     using S = R;
     static constexpr bool kPdev = PD;
+    static constexpr bool kGodd = false;
     template <int i>
     __device__ __forceinline__ static R dec_h(S v) { return v; }
     template <int i>
@@ -56,9 +57,12 @@ struct CodecId {
     }
 };
 
-// 16-bit storage of scaled deviations from the lattice weights, FP32
-// arithmetic.  h_i is held as t = 2 h_i / w_i - 1 (bulk heavy phase t = 1,
-// bulk light phase t = -1, both exact); g_i as g_i S / w_i (g_i is already a
+// 16-bit storage of scaled populations, FP32 arithmetic.  h_i is held as
+// t = h_i / w_i (bulk heavy phase t = 1, bulk light phase t = 0, both exact).
+// Near t = 0 a 16-bit float is much finer than near 1, and that is where it
+// matters: in the light phase rho = rho_a + phi (rho_w - rho_a) with rho_a
+// ~ 1e-3, so an error of 1e-4 in phi there is a 10 % error in rho and in
+// everything divided by it.  g_i is held as g_i S / w_i (g_i is already a
 // deviation: g_eq_i = Gamma_i - w_i + ...), with S = 1024 for FP16 to keep
 // small values out of the subnormal range and S = 1 for BF16; the rest
 // population of g is held without its P^n / (rho_ref T) part (kPdev).
@@ -85,17 +89,22 @@ struct CodecDev {
     using S = H;
     using B = Codec16<H>;
     static constexpr bool kPdev = true;
+    // BF16 (8 significant bits): g is stored without its first-order odd part
+    // w_i c_i . V_g (V_g per site, kept beside the populations in FP32), so
+    // what is rounded to 16 bits is the small remainder (see lbm_split.cuh).
+    // FP16 meets the velocity bound without it and keeps the bandwidth.
+    static constexpr bool kGodd = !B::kHalf;
     template <int i>
     __device__ __forceinline__ static float dec_h(S v)
     {
-        constexpr float hw = (float)(L::w(i) * 0.5);
-        return (B::to_f(v) + 1.0f) * hw;
+        constexpr float w = (float)L::w(i);
+        return B::to_f(v) * w;
     }
     template <int i>
     __device__ __forceinline__ static S enc_h(float h)
     {
-        constexpr float iw = (float)(2.0 / L::w(i));
-        return B::from_f(h * iw - 1.0f);
+        constexpr float iw = (float)(1.0 / L::w(i));
+        return B::from_f(h * iw);
     }
     template <int i>
     __device__ __forceinline__ static float dec_g(S v)
@@ -167,6 +176,8 @@ struct SplitArgs {
     float4 *F_new;            // packed (u^{n+1}, P^{n+1})
     float4 *FB;               // packed (u^{n+1}, phi^{n+1})
     float *PiG;               // sum_i c_ia c_ib g_i of the pulled g, [3 or 6][N]
+    const float4 *G_old;      // BF16 storage: odd part V_g of g* of the current state (see lbm_split.cuh)
+    float4 *G_new;            // ... of the state being made
     const uint32_t *mask;
     int *err;
     int nx, ny, nz;
@@ -547,6 +558,25 @@ __device__ __forceinline__ long long state_off(const RA &a, long long idx)
     const uint32_t m = a.mask ? a.mask[idx] : 0u;
     const Nbr nb(idx, a.nx, a.ny, L::D == 3 ? a.nz : 1);
     return aa_state_off<L, i>(nb, idx, a.N, m, a.mask != nullptr, a.aa - 1);
+}
+
+// Completes BF16 g populations stored without their odd part into g*:
+// g*_i(x) = stored_i(x) + w_i c_i . V_g(x).
+template <class L, class C>
+__global__ void __launch_bounds__(128) fold_g_kernel(const ReadArgs<float, typename C::S> a, typename C::S *g,
+                                                     const float4 *__restrict__ G)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= a.N) return;
+    if (a.mask && (a.mask[idx] & kSolidBit)) return;
+    const float4 v4 = G[idx];
+    const float v[3] = {v4.x, v4.y, v4.z};
+    static_for<1, L::Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const long long off = state_off<L, i>(a, idx);
+        const float gv = C::template dec_g<i>(g[off]);
+        g[off] = C::template enc_g<i>(gv + float(L::w(i)) * dot_c<L, i>(v));
+    });
 }
 
 template <class L, class R, class C, bool HAS_MASK>

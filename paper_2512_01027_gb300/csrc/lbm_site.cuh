@@ -330,11 +330,13 @@ __host__ __device__ constexpr int pig_slot(int a, int b)
     return D == 3 ? (a == 0 ? b : (a == 1 ? 2 + b : 5)) : (a == 0 ? b : 2);
 }
 
-template <class L, bool INIT, bool PDEV, bool GMOM = false>
+// GODD: g* is returned without its odd first-order part w_i c_i . V_g, and
+// V_g = u/T + F/(rho T) + sigma grad rho/(rho^2 T) is returned in vgout.
+template <class L, bool INIT, bool PDEV, bool GMOM = false, bool GODD = false>
 __device__ __forceinline__ void collide_pairs(const SiteConsts<float> &k, float phi, float phihat, float rho,
                                               float P, const float (&u)[3], const float (&gphi)[3], float lphi,
                                               const float (&gu)[3][3], const float *hp, const float *gp, float *hs,
-                                              float *gs, const float *pig = nullptr)
+                                              float *gs, const float *pig = nullptr, float *vgout = nullptr)
 {
     constexpr int D = L::D;
     constexpr int NP = (L::Q - 1) / 2;
@@ -407,6 +409,11 @@ __device__ __forceinline__ void collide_pairs(const SiteConsts<float> &k, float 
         Vh[a] = 3.f * phi * u[a] + theta_tot * n[a];
         Vg[a] = 3.f * u[a] + F[a] * kF + sg[a] * kS;
     });
+    if constexpr (GODD) {
+        vgout[0] = Vg[0];
+        vgout[1] = Vg[1];
+        vgout[2] = Vg[2];
+    }
     const float Eh0 = phi * (1.f - 1.5f * uu);
     const float Eg0 = bdiv - 1.5f * uu;
     const float p45 = 4.5f * phi;
@@ -491,8 +498,13 @@ __device__ __forceinline__ void collide_pairs(const SiteConsts<float> &k, float 
                 });
             });
             const float e = eg[p] + om * (float(L::w(i)) * 4.5f) * contr;
-            gs[i] = e + og[p];
-            gs[i + 1] = e - og[p];
+            if constexpr (GODD) {
+                gs[i] = e;
+                gs[i + 1] = e;
+            } else {
+                gs[i] = e + og[p];
+                gs[i + 1] = e - og[p];
+            }
         });
     }
 }

@@ -104,6 +104,13 @@ __device__ __forceinline__ IX write_idx(IX N, const Nbr32 &nb, int idx, uint32_t
 // collision launch the packed (u, phi) words of the new step and the second
 // moments sum_i c_ia c_ib g_i of the pulled g, which is all the filter
 // collision needs of g, so the collision launch pulls h only.
+//
+// BF16 storage: in the light phase the odd part of g*, w_i c_i . V_g with
+// V_g = u/T + F/(rho T) + sigma grad rho/(rho^2 T), is hundreds of times the
+// velocity it leaves after the pull (F/rho and grad P/rho nearly cancel), so
+// rounding g* to 8 significant bits would swamp u.  The collision launch stores g*
+// without that part, in 16 bits, and V_g per site in FP32; the next pull adds
+// w_i c_i . V_g of the site the population left back.
 template <class R>
 inline constexpr bool kPacked = std::is_same<R, float>::value;
 
@@ -125,6 +132,11 @@ __device__ __forceinline__ void moments_site(const SplitArgs<R, typename C::S> &
     if constexpr (kPacked<R>) P0 = a.F_old[idx].w;
     else P0 = a.P_old[idx];
     R sum_wcu = R(0);
+    [[maybe_unused]] float vgown[3];
+    if constexpr (kPacked<R> && C::kGodd) {
+        const float4 v4 = a.G_old[idx];
+        vgown[0] = v4.x; vgown[1] = v4.y; vgown[2] = v4.z;
+    }
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         const IX e = read_idx<L, MODE, i, IX>(N, nb, idx, m, HAS_MASK);
@@ -140,6 +152,14 @@ __device__ __forceinline__ void moments_site(const SplitArgs<R, typename C::S> &
                 const float4 f = a.F_old[src];
                 Pn[i] = bb ? P0 : f.w;
                 un[0] = f.x; un[1] = f.y; un[2] = f.z;
+                if constexpr (C::kGodd) {
+                    // add back the odd part w_i c_i . V_g of the site the population
+                    // left (bounce-back: g*_{-i}(x), whose part is - w_i c_i . V_g(x))
+                    const float4 v4 = a.G_old[src];
+                    const float vs[3] = {v4.x, v4.y, v4.z};
+                    const float corr = bb ? -dot_c<L, i>(vgown) : dot_c<L, i>(vs);
+                    gp[i] = gp[i] + float(L::w(i)) * corr;
+                }
             } else {
                 Pn[i] = bb ? P0 : a.P_old[src];
                 static_for<0, 3>([&](auto A) {
@@ -258,8 +278,10 @@ __device__ __forceinline__ void collide_site(const SplitArgs<R, typename C::S> &
             constexpr int j = decltype(J)::value;
             pm[j] = ld_maybe_cg<CG>(a.PiG + eidx<IX>(j, N, idx));
         });
-        collide_pairs<L, false, C::kPdev, true>(a.k, phi, phihat, rho, P, u, gphi, lphi, gu, hp, nullptr, hs, gs,
-                                               pm);
+        float vg[3];
+        collide_pairs<L, false, C::kPdev, true, C::kGodd>(a.k, phi, phihat, rho, P, u, gphi, lphi, gu, hp, nullptr,
+                                                         hs, gs, pm, vg);
+        if constexpr (C::kGodd) a.G_new[idx] = make_float4(vg[0], vg[1], vg[2], 0.f);
     } else {
         R gp[Q];
         static_for<0, Q>([&](auto I) {

@@ -6,7 +6,10 @@ surface tension, number of steps).  The server
 * takes requests as they arrive (arrival times in seconds from the start),
 * builds each request's initial fields on host threads while the GPU works,
 * admits requests first-come first-served while their device footprint
-  (``estimate_footprint``) fits in the HBM budget and a member slot is free,
+  (``estimate_footprint``) fits in the HBM budget, a member slot is free and
+  the sites of the admitted lattices stay within ``max_active_sites`` (one
+  large lattice already fills the GPU: sharing it among many large lattices
+  only stretches every one of them; small lattices still run many at once),
 * advances all admitted lattices together through one ``Batch`` (two kernel
   launches per time step for the whole set, chunks replayed as CUDA graphs),
   each lattice by exactly its own number of steps,
@@ -79,9 +82,10 @@ class Server:
 
     def __init__(self, lattice: str = "D3Q27", storage: str = "f16", inplace: bool = True, chunk: int = 16,
                  max_members: int = 64, hbm_budget: int | None = None, prep_threads: int = 4,
-                 keep_fields: bool = False, stream=None):
+                 keep_fields: bool = False, stream=None, max_active_sites: int | None = None):
         self.lattice, self.storage, self.inplace = lattice, storage, bool(inplace)
         self.chunk, self.max_members = int(chunk), int(max_members)
+        self.max_active_sites = max_active_sites
         self.keep_fields = keep_fields
         if hbm_budget is None:
             import torch
@@ -108,6 +112,7 @@ class Server:
         active = []                            # (request, Lattice, bytes, admitted)
         stats = ServeStats()
         used = 0
+        sites = 0
         launches0 = self.batch.info()[1]
         with ThreadPoolExecutor(max_workers=self.prep_threads) as pool:
             t0 = clock()
@@ -124,6 +129,9 @@ class Server:
                         raise ValueError(f"request {r.rid} needs {need} bytes, more than the HBM budget")
                     if used + need > self.hbm_budget:
                         break
+                    n_sites = r.edge ** 3
+                    if active and self.max_active_sites is not None and sites + n_sites > self.max_active_sites:
+                        break
                     if active and not fut.done():
                         break                  # keep the GPU busy; admit it next round
                     c = fut.result()
@@ -134,6 +142,7 @@ class Server:
                     L.init_fields(c.phi0, c.P0, c.u0)
                     self.batch.add(L, r.steps)
                     used += need
+                    sites += n_sites
                     active.append((r, L, need, clock() - t0))
                 stats.peak_members = max(stats.peak_members, len(active))
                 stats.peak_bytes = max(stats.peak_bytes, used)
@@ -152,6 +161,7 @@ class Server:
                         self.batch.remove(L)
                         L.close()
                         used -= need
+                        sites -= L.N
                         stats.results.append(Served(r.rid, r.arrival, t_adm, t_fin, r.steps, L.N,
                                                     out if self.keep_fields else None))
                     else:

@@ -110,12 +110,15 @@ def test_footprint_estimate_needs_no_device():
     """Admission control sizes a lattice before creating it: populations
     (2 sets in place, 4 ping-pong), P, u (two each), phi; with FP32
     arithmetic the packed (u, P) words (two), the packed (u, phi) words and
-    the six second moments of g; scratch, mask."""
+    the six second moments of g; with BF16 storage the odd part of g (two);
+    scratch, mask."""
     N = 32 ** 3
     scratch = 8 * (1024 * 8 + 64) + 256
     packed = (2 * 16 + 16 + 4 * 6) * N + 4 * (2 + 32)
     got = lbm.estimate_footprint("D3Q27", (32, 32, 32), storage="f16", inplace=1)
     assert got == 2 * 27 * N * 2 + 9 * N * 4 + packed + scratch
+    got = lbm.estimate_footprint("D3Q27", (32, 32, 32), storage="bf16", inplace=1)
+    assert got == 2 * 27 * N * 2 + 9 * N * 4 + packed + 2 * 16 * N + scratch
     got = lbm.estimate_footprint("D3Q27", (32, 32, 32), periodic=(1, 1, 0), storage="f32")
     assert got == 4 * 27 * N * 4 + 9 * N * 4 + packed + scratch + 4 * N
     got = lbm.estimate_footprint("D2Q9", (16, 8, 1), storage="f64")

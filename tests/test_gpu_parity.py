@@ -192,12 +192,11 @@ def test_short_horizon_f32(lbm, lat):
     assert np.abs(f1 - f2).max() <= 1e-5
 
 
-@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-4), ("f16", 1e-2)])
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-4), ("f16", 1e-2), ("bf16", 1e-2)])
 def test_laplace_pressure_long_run(lbm, storage, tol):
     """64^2 droplet, 10000 steps: the Laplace jump dP = P_in - P_out of the
-    GPU path against the oracle's (FP64 bit for bit; FP32 measured 3.1e-5;
-    FP16 storage measured 2.3e-3, inside the 1% target).  BF16 storage misses
-    it (dP 22% high) and is not asserted here."""
+    GPU path against the oracle's (FP64 bit for bit; FP32 measured 7.6e-6;
+    FP16 storage 1.6e-3 and BF16 storage 2.7e-3, inside the 1% target)."""
     c = W.droplet_2d(64, 16.0)
     _, g = run_gpu(lbm, c, 10000, storage=storage)
     _, o = run_oracle(c, 10000)
@@ -353,20 +352,21 @@ def test_zchunk_does_not_change_results(lbm):
 
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
 def test_reduced_storage_short_horizon(lbm, storage):
-    """16-bit storage against the FP64 oracle over 5 steps.  phi: each step
-    rounds t = 2h/w - 1 to half a 16-bit spacing (2^-12 FP16, 2^-9 BF16), so
-    |dphi| <= steps * 0.5 * spacing (measured 1.9e-4 / 1.9e-3).  Velocity:
-    in the light phase g carries F/rho and sigma grad(rho)/rho^2, 1/rho_a =
-    1000 times larger than u, so 16-bit relative precision on g shows up
-    magnified in u (measured 1.4e-3 / 3.0e-2 of max|u|)."""
+    """16-bit storage against the FP64 oracle over 5 steps (3D droplet over a
+    film with walls).  phi: each step rounds t = h/w to half a 16-bit spacing
+    (at most 2^-11 FP16, 2^-8 BF16, for t < 2), so |dphi| <= steps * half
+    (measured 2.6e-4 / 2.0e-3).  Velocity to 1e-3 of max|u| (measured 2.7e-4
+    FP16, 3.4e-4 BF16): h is stored as h/w, whose 16-bit spacing is finest
+    near phi = 0, where the light phase's rho = rho_a + phi (rho_w - rho_a)
+    is most sensitive to phi; BF16 also keeps the odd part of g in FP32."""
     c = small_3d("D3Q27", nx=24, ny=20, nz=18)
     n = 5
     _, g = run_gpu(lbm, c, n, storage=storage)
     _, o = run_oracle(c, n)
     (f1, P1, u1), (f2, P2, u2) = g, o
-    half = 2.0 ** -12 if storage == "f16" else 2.0 ** -9
+    half = 2.0 ** -11 if storage == "f16" else 2.0 ** -8
     assert np.abs(f1 - f2).max() <= n * half
-    assert np.abs(u1 - u2).max() <= (5e-3 if storage == "f16" else 1e-1) * np.abs(u2).max()
+    assert np.abs(u1 - u2).max() <= 1e-3 * np.abs(u2).max()
     assert np.abs(P1 - P2).max() <= (1e-3 if storage == "f16" else 1e-2) * np.abs(P2).max()
 
 

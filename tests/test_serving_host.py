@@ -1,0 +1,101 @@
+"""Host logic of the serving loop (admission, continuous batching, retiring,
+latency accounting) with the GPU objects replaced by fakes: no device
+needed.  The fakes count steps exactly like the batch does (each member
+advances by min(n, its remaining budget))."""
+import pytest
+
+import workloads as W
+from paper_2512_01027_gb300 import serving
+
+
+class FakeLattice:
+    def __init__(self, lattice, shape, **kw):
+        self.N = shape[0] * shape[1] * shape[2]
+        self.steps_done = 0
+        self.closed = False
+
+    def init_fields(self, phi, P, u):
+        pass
+
+    def read_fields(self):
+        return (self.steps_done,)
+
+    def close(self):
+        self.closed = True
+
+
+class FakeBatch:
+    log = []
+
+    def __init__(self, lattice, storage):
+        self.rem = {}
+
+    def set_tuning(self, chunk=16, use_graph=True):
+        pass
+
+    def add(self, L, steps):
+        self.rem[id(L)] = [L, steps]
+        FakeBatch.log.append(("add", len(self.rem)))
+
+    def remove(self, L):
+        del self.rem[id(L)]
+
+    def step(self, n):
+        for L, r in self.rem.values():
+            t = min(n, r)
+            L.steps_done += t
+        for v in self.rem.values():
+            v[1] -= min(n, v[1])
+        return sum(1 for v in self.rem.values() if v[1] == 0)
+
+    def remaining(self, L):
+        return self.rem[id(L)][1]
+
+    def info(self):
+        return len(self.rem), 0
+
+    def close(self):
+        pass
+
+
+@pytest.fixture
+def fake(monkeypatch):
+    monkeypatch.setattr(serving, "Lattice", FakeLattice)
+    monkeypatch.setattr(serving, "Batch", FakeBatch)
+    monkeypatch.setattr(serving, "_prepare", lambda r: W.Case("c", "D3Q27", (r.edge,) * 3, W.base_params(), 0, 0, 0,
+                                                             (1, 1, 1), None, r.steps))
+    FakeBatch.log = []
+
+
+def trace(n=12):
+    return W.request_trace(n=n, rate=1e9, edges=(16, 20, 24), steps_range=(7, 40))
+
+
+def test_every_request_gets_exactly_its_steps(fake):
+    reqs = trace()
+    S = serving.Server("D3Q27", "f16", chunk=5, keep_fields=True, hbm_budget=1 << 40)
+    st = S.run(reqs)
+    assert [r.rid for r in st.results] == sorted(r.rid for r in reqs)
+    for r, res in zip(sorted(reqs, key=lambda q: q.rid), st.results):
+        assert res.fields == (r.steps,)
+        assert res.arrival <= res.admitted <= res.finished
+
+
+def test_admission_limits(fake):
+    reqs = trace(20)
+    one = serving.estimate_footprint("D3Q27", (24, 24, 24), storage="f16", inplace=1)
+    S = serving.Server("D3Q27", "f16", chunk=5, hbm_budget=3 * one, max_members=2)
+    st = S.run(reqs)
+    assert len(st.results) == 20
+    assert st.peak_members <= 2 and st.peak_bytes <= 3 * one
+    S = serving.Server("D3Q27", "f16", chunk=5, hbm_budget=1 << 40, max_active_sites=2 * 24 ** 3)
+    st = S.run(reqs)
+    assert len(st.results) == 20
+    assert max(n for _, n in FakeBatch.log) <= 8          # never more than the site cap allows of 16^3 lattices
+
+
+def test_site_cap_still_admits_one_large_request(fake):
+    reqs = W.request_trace(n=3, rate=1e9, edges=(32,), steps_range=(5, 9))
+    S = serving.Server("D3Q27", "f16", chunk=4, hbm_budget=1 << 40, max_active_sites=1000)
+    st = S.run(reqs)
+    assert len(st.results) == 3 and st.peak_members == 1
