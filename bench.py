@@ -148,14 +148,15 @@ def alg_bytes_per_site(Q: int, D: int, store_bytes: int, field_bytes: int) -> in
 
 def cpu_baseline(reps_target_s: float = 10.0):
     """The FP64 oracle as it stands, on the host cores, on a bounded sample of
-    the workload: the same droplet-on-film case at 64^3 (R = 8), 24 steps."""
+    the workload: the same droplet-on-film case at 64^3 (R = 8), 320 steps
+    (about 10 s on 16 cores)."""
     import oracle
 
     c = W.droplet_film_3d(n=64, R=8.0, film=8.0, gap=8.0, uz=-0.05, noise=1e-4)
     o = oracle.Oracle("D3Q27", c.shape, oracle.make_params(**c.params), periodic=c.periodic, solid=c.solid)
     o.init(c.phi0, c.P0, c.u0)
     o.step(1)
-    steps = 24
+    steps = 320
     t0 = time.perf_counter()
     o.step(steps)
     dt = time.perf_counter() - t0
