@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--n", type=int, default=256, help="grid edge of the workload")
     ap.add_argument("--storage", default="f32")
     ap.add_argument("--variant", type=int, default=0,
-                    help="0 automatic (split form), 1 fused plane-synchronous, 2 fused pipelined, 3 split form")
+                    help="0 automatic (split form), 1 fused plane-synchronous, 2 fused pipelined, 3 split form, "
+                         "4 persistent split form")
     ap.add_argument("--inplace", action="store_true", help="one population store, AA streaming")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
