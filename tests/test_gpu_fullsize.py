@@ -1,0 +1,64 @@
+"""Parity at the benchmark's full size, in the launch configuration bench.py
+times: 256^3 D3Q27 droplet impact on a film (16.8 M sites, walls at z = 0,
+255), FP32 storage, split form, ping-pong store; and the in-place store.
+
+The FP64 oracle takes a few seconds a step at this size on the host cores,
+so the whole lattice is compared after two steps (short horizon: the FP32
+bounds of the short-horizon tests), together with the conserved phase mass.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 2
+
+
+def _host_gb():
+    try:
+        return os.sysconf("SC_PHYS_PAGES") * os.sysconf("SC_PAGE_SIZE") / 1e9
+    except (ValueError, OSError):
+        return 0.0
+
+
+@pytest.fixture(scope="module")
+def case_and_oracle():
+    if _host_gb() < 64:
+        pytest.skip("the FP64 oracle needs about 23 GB of host memory at 256^3")
+    n = 256
+    c = W.droplet_film_3d(n=n, R=n / 8.0, film=n / 8.0, uz=-0.05, noise=1e-4)   # the benchmark's workload
+    o = oracle.Oracle(c.lattice, c.shape, oracle.make_params(**c.params), periodic=c.periodic, solid=c.solid)
+    o.init(c.phi0, c.P0, c.u0)
+    o.step(STEPS)
+    f = o.fields()
+    del o
+    return c, f
+
+
+@pytest.mark.parametrize("inplace", [0, 1])
+def test_benchmark_workload_full_size(lbm, case_and_oracle, inplace):
+    c, (phi_o, P_o, u_o) = case_and_oracle
+    prm = {k: v for k, v in c.params.items() if k != "g_ext"}
+    L = lbm.Lattice(c.lattice, c.shape, periodic=c.periodic, solid=c.solid, storage="f32",
+                    g_ext=c.params["g_ext"], inplace=inplace, **prm)
+    L.init_fields(c.phi0, c.P0, c.u0)
+    L.step(STEPS)
+    L.check()
+    phi, P, u = L.read_fields()
+    assert np.all(np.isfinite(phi)) and np.all(np.isfinite(P)) and np.all(np.isfinite(u))
+    dphi = np.abs(phi - phi_o).max()
+    du = np.abs(u - u_o).max() / np.abs(u_o).max()
+    dP = np.abs(P - P_o).max() / np.abs(P_o).max()
+    assert dphi <= 1e-5, f"phi {dphi:.3e}"
+    assert du <= 1e-5, f"u {du:.3e} of max|u|"
+    # the pressure here is the falling droplet's (rho c_s u), not the Laplace jump
+    assert dP <= 1e-6, f"P {dP:.3e} of max|P| = {np.abs(P_o).max():.3e}"
+    # phase mass: the FP64 sum of the GPU's phi equals the oracle's to FP32 rounding per site
+    mass = L.reduce()["mass"]
+    assert abs(mass / phi_o.sum() - 1) <= 1e-6
+    L.close()
