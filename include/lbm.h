@@ -51,7 +51,7 @@ extern "C" {
 #define LBM_ERR_OOM 2           /* device allocation failed (cudaMalloc or the allocator hook) */
 #define LBM_ERR_CUDA 3          /* a CUDA runtime call or kernel launch failed */
 #define LBM_ERR_NONFINITE 4     /* a step produced a non-finite phi, P or u */
-#define LBM_ERR_UNSUPPORTED 5   /* valid request this build does not implement */
+#define LBM_ERR_UNSUPPORTED 5   /* a valid request the library does not implement */
 #define LBM_ERR_TIMEOUT 6       /* a bounded wait inside a kernel ran out; the step's results are invalid */
 
 typedef struct lbm_ctx *lbm_handle;

@@ -19,7 +19,7 @@
  *   S4  h_eq and the phase-field BGK collision               (Eq. LB_phi_filter_col, h_eq, Gamma_i)
  *   S5  g_eq, Pi and the filter collision                     (Eq. BGK_LBeq_hydroeq g_eq, Eqs. momentum_flux0/1, LB_filter_col)
  *
- * Readings where the paper is silent or ambiguous (each listed in the design doc):
+ * Readings where the paper is silent or ambiguous:
  *   - K_i uses P^n (previous step) at x and x - c_i; the omega-term of P uses
  *     u^n(x - c_i), the velocity of the previous step (one LKS pass started
  *     from the previous step).  Using u^{n+1} there instead makes the liquid
