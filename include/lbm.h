@@ -181,7 +181,12 @@ int lbm_probe(lbm_handle h, int64_t n, const int64_t *sites, double *h_pop, doub
  * counter).  lbm_state_bytes gives the size; save/load copy through a host
  * buffer of exactly that size.  A state loads only into a handle of the same
  * lattice, grid, storage and layout (in-place or not); anything else is
- * LBM_ERR_INVALID_ARG and leaves the handle unchanged. */
+ * LBM_ERR_INVALID_ARG and leaves the handle unchanged.
+ * With BF16 storage the split form keeps part of g (its first-order odd
+ * part) in FP32 beside the populations; saving a state first folds it into
+ * the stored BF16 populations (one rounding), so the handle continues from
+ * the saved state exactly as one that loads it.  Reading populations
+ * (lbm_get_state, lbm_probe) adds that part on the fly and changes nothing. */
 int lbm_state_bytes(lbm_handle h, size_t *bytes);
 int lbm_save_state(lbm_handle h, void *host_buf, size_t bytes);
 int lbm_load_state(lbm_handle h, const void *host_buf, size_t bytes);

@@ -413,14 +413,15 @@ struct Impl {
         a.cP = R(c->consts.cP);
         a.aa = c->inplace ? 1 + (int)(c->steps % 2) : 0;
         a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
+        a.G = nullptr;
+        if constexpr (kPacked<R> && C::kGodd)
+            if (c->g_deferred) a.G = static_cast<const float4 *>(c->fg[c->cur]);
         return a;
     }
 
     static int read(lbm_ctx *c, double *d_phi, double *d_P, double *d_u, double *d_hpop, double *d_gpop)
     {
         if (const int rs = sync_soa(c); rs != LBM_OK) return rs;
-        if (d_gpop)   // individual g*: complete the deferred odd part
-            if (const int rf = fold(c); rf != LBM_OK) return rf;
         ReadArgs<R, S> a = read_args(c);
         a.phi_out = d_phi; a.P_out = d_P; a.u_out = d_u; a.hpop_out = d_hpop; a.gpop_out = d_gpop;
         const int threads = 256;
@@ -465,8 +466,6 @@ struct Impl {
     static int probe(lbm_ctx *c, const long long *d_sites, int n, double *d_h, double *d_g, double *d_P, double *d_u)
     {
         if (const int rs = sync_soa(c); rs != LBM_OK) return rs;
-        if (d_g)
-            if (const int rf = fold(c); rf != LBM_OK) return rf;
         ReadArgs<R, S> a = read_args(c);
         const int threads = 128;
         probe_kernel<L, R, C><<<(n + threads - 1) / threads, threads, 0, c->stream>>>(a, d_sites, n, d_h, d_g, d_P, d_u);

@@ -544,11 +544,26 @@ struct ReadArgs {
     const uint32_t *mask;
     double *phi_out, *P_out, *u_out;   // u_out: [3][N]
     double *hpop_out, *gpop_out;       // optional decoded populations [Q][N]
+    const float4 *G;                   // BF16 storage: deferred odd part of g* (added when read), or NULL
     long long N;
     R cP;
     int aa;                            // 0: ping-pong layout; 1 + parity: in-place AA layout
     int nx, ny, nz;
 };
+
+// The deferred odd part w_i c_i . V_g(x) of g*_i(x), 0 when nothing is deferred.
+template <class L, int i, class RA>
+__device__ __forceinline__ float g_deferred(const RA &a, long long idx)
+{
+    if constexpr (i == 0) {
+        return 0.f;
+    } else {
+        if (!a.G) return 0.f;
+        const float4 v4 = a.G[idx];
+        const float v[3] = {v4.x, v4.y, v4.z};
+        return float(L::w(i)) * dot_c<L, i>(v);
+    }
+}
 
 // Offset of the post-collision f*_i(x) in the current state.
 template <class L, int i, class RA>
@@ -614,7 +629,9 @@ __global__ void __launch_bounds__(256) read_kernel(const ReadArgs<R, typename C:
             if (a.hpop_out) a.hpop_out[(long long)i * a.N + idx] =
                 solid ? 0.0 : (double)C::template dec_h<i>(a.h[state_off<L, i>(a, idx)]);
             if (a.gpop_out) a.gpop_out[(long long)i * a.N + idx] =
-                solid ? 0.0 : (double)C::template view_g<i>(a.g[state_off<L, i>(a, idx)], P, a.cP);
+                solid ? 0.0
+                      : (double)(C::template view_g<i>(a.g[state_off<L, i>(a, idx)], P, a.cP) +
+                                 g_deferred<L, i>(a, idx));
         });
     }
 }
@@ -649,7 +666,9 @@ __global__ void __launch_bounds__(128) probe_kernel(const ReadArgs<R, typename C
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         if (hp) hp[(long long)j * Q + i] = (double)C::template dec_h<i>(a.h[state_off<L, i>(a, idx)]);
-        if (gp) gp[(long long)j * Q + i] = (double)C::template view_g<i>(a.g[state_off<L, i>(a, idx)], Ps, a.cP);
+        if (gp)
+            gp[(long long)j * Q + i] =
+                (double)(C::template view_g<i>(a.g[state_off<L, i>(a, idx)], Ps, a.cP) + g_deferred<L, i>(a, idx));
     });
 }
 

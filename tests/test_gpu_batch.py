@@ -49,7 +49,7 @@ def test_batch_f64_matches_oracle(lbm):
             assert np.array_equal(x, y)
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 def test_alone_vs_mixed_bitwise(lbm, storage):
     """A lattice stepped alone in a batch and stepped among others (which
     join late, leave early and use the other store layout) ends bit for bit

@@ -117,21 +117,25 @@ def test_inplace_state_matches_ping_pong(lbm, steps):
     assert np.array_equal(ra["momentum"], rb["momentum"])
 
 
-def test_inplace_checkpoint_resume(lbm):
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_inplace_checkpoint_resume(lbm, storage):
+    """A checkpoint taken after an odd step count (shifted AA layout; with
+    BF16 also the deferred odd part of g, folded into the populations when
+    saved) resumes bit for bit."""
     c = small_3d("D3Q27")
-    L1 = make(lbm, c, "f32", inplace=1)
+    L1 = make(lbm, c, storage, inplace=1)
     L1.step(13)                                   # odd: shifted AA layout
     blob = L1.save_state()
     L1.step(8)
     want = L1.read_fields()
-    L2 = make(lbm, c, "f32", inplace=1)
+    L2 = make(lbm, c, storage, inplace=1)
     L2.load_state(blob)
     assert L2.steps_done == 13
     L2.step(8)
     for x, y in zip(want, L2.read_fields()):
         assert np.array_equal(x, y)
     # a ping-pong handle refuses the in-place layout and keeps its own state
-    L3 = make(lbm, c, "f32")
+    L3 = make(lbm, c, storage)
     before = L3.read_fields()
     with pytest.raises(lbm.LbmError) as e:
         L3.load_state(blob)
@@ -194,3 +198,21 @@ def test_persistent_refused_for_f64(lbm):
     with pytest.raises(lbm.LbmError) as e:
         L.set_tuning(4, 0)
     assert e.value.code == lbm.LBM_ERR_UNSUPPORTED
+
+
+def test_bf16_population_reads_change_nothing(lbm):
+    """With BF16 storage part of g is kept beside the populations; reading
+    the populations (get_state, probe) adds it on the fly, so a handle that
+    was read continues bit for bit like one that was not."""
+    c = small_3d("D3Q27")
+    a = make(lbm, c, "bf16")
+    b = make(lbm, c, "bf16")
+    a.step(5)
+    b.step(5)
+    h1, g1, _, _ = a.get_state()
+    a.probe(np.arange(0, a.N, 97))
+    assert np.all(np.isfinite(g1))
+    a.step(6)
+    b.step(6)
+    for x, y in zip(a.read_fields(), b.read_fields()):
+        assert np.array_equal(x, y)
