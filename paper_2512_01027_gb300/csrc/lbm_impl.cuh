@@ -293,7 +293,7 @@ struct Impl {
             p.ctl = c->pctl;
             p.nz = L::D == 3 ? c->nz : 1;
             p.nxy = (int)(c->N / p.nz);
-            p.bpp = (p.nxy + kSplitThreads - 1) / kSplitThreads;
+            p.bpp = (p.nxy + kSplitThreads * kPersistSpan - 1) / (kSplitThreads * kPersistSpan);
             p.zper = L::D == 3 ? c->periodic[2] : 1;
             p.lag = kPersistLag;
             p.err = c->d_err;

@@ -4,7 +4,7 @@
 // second moments of g, the pulled h a second time) is still in L2 when it is
 // read.
 //
-// Work items are blocks of kSplitThreads consecutive sites of one z-plane.
+// Work items are kPersistSpan x kSplitThreads consecutive sites of one z-plane.
 // Blocks take items from a ticket counter in this order of plane units
 // (M = moments, C = collision, lag G >= 1 planes):
 //   M(0) .. M(G), then M(1 + G), C(1), M(2 + G), C(2), ..., C(nz - 1), C(0)
@@ -39,6 +39,7 @@ struct PersistArgs {
 
 constexpr long long kPersistMaxSpin = 1LL << 24;   // >= 1 s of polling
 constexpr int kPersistLag = 2;
+constexpr int kPersistSpan = 2;   // consecutive 128-site blocks per work item
 
 // Plane unit u of the schedule: phase 0 = moments, 1 = collision.
 __device__ __forceinline__ void persist_unit(int u, int nz, int lag, int &phase, int &plane)
@@ -104,18 +105,23 @@ __global__ void __launch_bounds__(kSplitThreads, kSplitMinBlocks)
         const int unit = t / p.bpp, blk = t - unit * p.bpp;
         int phase, plane;
         persist_unit(unit, p.nz, p.lag, phase, plane);
-        const int off = blk * kSplitThreads + (int)threadIdx.x;
-        const bool in = off < p.nxy;
-        const int idx = plane * p.nxy + off;
         if (phase == 0) {
-            if (in) moments_site<L, float, C, HAS_MASK, MODE, uint32_t>(a, idx);
+            for (int k = 0; k < kPersistSpan; ++k) {
+                const int off = (blk * kPersistSpan + k) * kSplitThreads + (int)threadIdx.x;
+                if (off < p.nxy) moments_site<L, float, C, HAS_MASK, MODE, uint32_t>(a, plane * p.nxy + off);
+            }
             __threadfence();
             __syncthreads();
             if (threadIdx.x == 0) atomicAdd(p.ctl + 2 + plane, 1);
         } else {
             if (threadIdx.x == 0) s_ok = persist_wait(p, plane);
             __syncthreads();
-            if (s_ok && in) collide_site<L, float, C, HAS_MASK, MODE, uint32_t, true>(a, idx);
+            if (s_ok)
+                for (int k = 0; k < kPersistSpan; ++k) {
+                    const int off = (blk * kPersistSpan + k) * kSplitThreads + (int)threadIdx.x;
+                    if (off < p.nxy)
+                        collide_site<L, float, C, HAS_MASK, MODE, uint32_t, true>(a, plane * p.nxy + off);
+                }
         }
     }
 }
