@@ -10,8 +10,9 @@
  *     LKS-mapped moments (Eq. Kiterm and the P, u definitions), the equilibrium of
  *     Eq. BGK_LBeq_hydroeq (surface-tension force, density-gradient stress term,
  *     bulk term B) and the filter collision (Eqs. momentum_flux0/1, LB_filter_col).
- * One call of lbm_step advances both populations by one time step per site in a
- * single fused CUDA kernel launch.
+ * One time step of lbm_step advances both populations at every site, by default
+ * in two kernel launches (the split form: moments, then stencils and
+ * collisions; see lbm_set_tuning for the fused and persistent forms).
  *
  * Conventions (all entry points):
  *   - Every function returns an int status: LBM_OK (0) or one of the LBM_ERR_*

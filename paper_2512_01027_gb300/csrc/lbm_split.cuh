@@ -2,14 +2,17 @@
 // site, no shared memory and no block-wide synchronisation.
 //
 //   moments_kernel  (S0, S1): pull both populations, phi = sum h_i, K_i,
-//                   u^{n+1}, P^{n+1}; write phi, u^{n+1}, P^{n+1}.
-//   collide_kernel  (S0, S2..S5): pull both populations again, stencils of
-//                   phi and u^{n+1} read from the fields the first launch
-//                   wrote (L1/L2 hits), both collisions, store.
+//                   u^{n+1}, P^{n+1}; write phi, u^{n+1}, P^{n+1} (FP32
+//                   arithmetic: as packed words, with the second moments of
+//                   the pulled g, see below).
+//   collide_kernel  (S0, S2..S5): stencils of phi and u^{n+1} read from what
+//                   the first launch wrote (L1/L2 hits), pull the populations
+//                   again (FP32 arithmetic: h only), both collisions, store.
 //
 // The grid-wide dependency between the moments and their stencils is the
 // launch boundary, so no halo is recomputed; the price is a second read of
-// the populations (704 instead of 464 B per FP32 D3Q27 site update).  The
+// populations and the hand-over between the launches (measured 633 instead
+// of 464 B per FP32 D3Q27 site update).  The
 // split form also admits in-place streaming: with the AA pattern a site
 // reads and writes one and the same set of population slots in every step,
 // so both launches can work on a single population store.
