@@ -59,7 +59,8 @@ __global__ void __launch_bounds__(kSplitThreads, 3)
     for (long long t = blockIdx.x; t < total; t += gridDim.x) {
         const int j = batch_find(mem, nmem, t);
         const int q = k & 1;
-        const SplitArgs<R, S> a = mem[j].a[q];
+        SplitArgs<R, S> a = mem[j].a[q];
+        a.seed += (unsigned)(k - q);   // a[q] holds the chunk's first steps; step k of the chunk
         const int mode = mem[j].mode[q];
         const long long lidx = (t - mem[j].first_item) * kSplitThreads + threadIdx.x;
         if (lidx >= a.N) continue;

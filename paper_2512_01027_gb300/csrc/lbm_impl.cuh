@@ -116,6 +116,7 @@ struct Impl {
         a.k = site_consts<R>(c->consts);
         a.phi = static_cast<R *>(c->phi);
         const int src = c->cur ^ flip, dst = 1 - src;
+        a.seed = (unsigned)(c->steps + flip);
         a.F_old = static_cast<const float4 *>(c->fa[src]);
         a.F_new = static_cast<float4 *>(c->fa[dst]);
         a.FB = static_cast<float4 *>(c->fb);

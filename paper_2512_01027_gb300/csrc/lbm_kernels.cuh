@@ -41,10 +41,13 @@ struct CodecId {
     using S = R;
     static constexpr bool kPdev = PD;
     static constexpr bool kGodd = false;
+    static constexpr bool kRound16 = false;
     template <int i>
     __device__ __forceinline__ static R dec_h(S v) { return v; }
     template <int i>
     __device__ __forceinline__ static S enc_h(R v) { return v; }
+    template <int i>
+    __device__ __forceinline__ static S enc_h_sr(R v, uint32_t) { return v; }
     template <int i>
     __device__ __forceinline__ static R dec_g(S v) { return v; }
     template <int i>
@@ -82,13 +85,47 @@ struct Codec16 {
         if constexpr (kHalf) return __float2half_rn(v);
         else return __float2bfloat16_rn(v);
     }
+    // Unbiased (stochastic) rounding: v goes to the 16-bit value above with
+    // probability (v - below) / (above - below), decided by r (uniform 32 bits).
+    // A v within FP32 noise (2^-20 relative) of a 16-bit value is that value:
+    // exact states (a fluid at rest) stay exact.
+    __device__ __forceinline__ static H from_f_sr(float v, uint32_t r)
+    {
+        const H n = from_f(v);
+        if (fabsf(v - to_f(n)) <= fabsf(v) * (1.0f / 1048576.0f)) return n;
+        H lo, hi;
+        if constexpr (kHalf) {
+            lo = __float2half_rd(v);
+            hi = __float2half_ru(v);
+        } else {
+            lo = __float2bfloat16_rd(v);
+            hi = __float2bfloat16_ru(v);
+        }
+        const float flo = to_f(lo), fhi = to_f(hi);
+        if (!(fhi > flo)) return lo;
+        const float p = (v - flo) / (fhi - flo);
+        return (float)(r >> 8) * (1.0f / 16777216.0f) < p ? hi : lo;
+    }
 };
+
+// 32-bit mixer (Wellons' "lowbias32") of a counter: the random bits of the
+// stochastic rounding, a function of (site, step) only.
+__device__ __forceinline__ uint32_t mix32(uint32_t x)
+{
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
 
 template <class L, class H>
 struct CodecDev {
     using S = H;
     using B = Codec16<H>;
     static constexpr bool kPdev = true;
+    static constexpr bool kRound16 = true;
     // BF16 (8 significant bits): g is stored without its first-order odd part
     // w_i c_i . V_g (V_g per site, kept beside the populations in FP32), so
     // what is rounded to 16 bits is the small remainder (see lbm_split.cuh).
@@ -105,6 +142,12 @@ struct CodecDev {
     {
         constexpr float iw = (float)(1.0 / L::w(i));
         return B::from_f(h * iw);
+    }
+    template <int i>
+    __device__ __forceinline__ static S enc_h_sr(float h, uint32_t r)
+    {
+        constexpr float iw = (float)(1.0 / L::w(i));
+        return B::from_f_sr(h * iw, r);
     }
     template <int i>
     __device__ __forceinline__ static float dec_g(S v)
@@ -125,6 +168,24 @@ struct CodecDev {
         else return dec_g<i>(v);
     }
 };
+
+// 16-bit storage: the rounding of the moving populations h_i (i != 0) is
+// taken up by the rest population before it is rounded in turn, so the
+// stored sum_i h_i of a site (its phi) carries one rounding instead of Q.
+// Without it, a liquid slightly above phi = 1 rounds down in every
+// direction at every step and the phase mass drifts.
+template <class L, class C, class R>
+__device__ __forceinline__ void compensate_h(R *hs)
+{
+    if constexpr (C::kRound16) {
+        R e = R(0);
+        static_for<1, L::Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            e = e + (C::template dec_h<i>(C::template enc_h<i>(hs[i])) - hs[i]);
+        });
+        hs[0] = hs[0] - e;
+    }
+}
 
 // cp.async helpers (LDGSTS: global -> shared without a register round trip)
 __device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
@@ -174,6 +235,7 @@ struct SplitArgs {
     R *phi;                   // phi^{n+1} [N]
     const float4 *F_old;      // packed (u^n, P^n) per site, FP32 arithmetic only (else NULL)
     float4 *F_new;            // packed (u^{n+1}, P^{n+1})
+    unsigned seed;            // steps taken before this one (stream of the stochastic rounding)
     float4 *FB;               // packed (u^{n+1}, phi^{n+1})
     float *PiG;               // sum_i c_ia c_ib g_i of the pulled g, [3 or 6][N]
     const float4 *G_old;      // BF16 storage: odd part V_g of g* of the current state (see lbm_split.cuh)
@@ -448,6 +510,7 @@ step_kernel(const StepArgs<R, typename C::S> a)
                     gp[i] = st_g[(ss * Q + i) * TI + ti];
                 });
                 collide<L, R, false, C::kPdev>(a.k, phi, phihat, rho, P, u, gphi, lphi, gu, hp, gp, hs, gs);
+                compensate_h<L, C>(hs);
                 const long long idx = (long long)zc * nx * ny + (long long)ys * nx + xs;
                 static_for<0, Q>([&](auto I) {
                     constexpr int i = decltype(I)::value;
@@ -521,6 +584,7 @@ __global__ void __launch_bounds__(128) init_kernel(const InitArgs<R, typename C:
     const R P = R(a.P0[idx]);
     R hs[Q], gs[Q];
     collide<L, R, true, C::kPdev>(a.k, phi, phihat, rho, P, u, gphi, lphi, gu, nullptr, nullptr, hs, gs);
+    compensate_h<L, C>(hs);
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         const long long off = (long long)(a.aa ? opp(i) : i) * a.N + idx;

@@ -295,10 +295,17 @@ __device__ __forceinline__ void collide_site(const SplitArgs<R, typename C::S> &
         });
         collide<L, R, false, C::kPdev>(a.k, phi, phihat, rho, P, u, gphi, lphi, gu, hp, gp, hs, gs);
     }
+    compensate_h<L, C>(hs);
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
         const IX e = write_idx<L, MODE, i, IX>(N, nb, idx, m, HAS_MASK);
-        a.dst_h[e] = C::template enc_h<i>(hs[i]);
+        if constexpr (i == 0 && C::kRound16) {
+            // the rest population carries the site's rounding: round it without
+            // bias, so a liquid just above phi = 1 does not lose mass step by step
+            a.dst_h[e] = C::template enc_h_sr<0>(hs[0], mix32((uint32_t)idx * 0x9e3779b9u ^ mix32(a.seed)));
+        } else {
+            a.dst_h[e] = C::template enc_h<i>(hs[i]);
+        }
         a.dst_g[e] = C::template enc_g<i>(gs[i]);
     });
     if (!(isfinite(phi) && isfinite(P) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2])))

@@ -262,6 +262,7 @@ step_kernel_v2(const StepArgs<R, typename C::S> a)
                 gp[i] = C::template dec_g<i>(src[(Q + i) * PL]);
             });
             collide<L, R, false, C::kPdev>(a.k, phi, phihat, rho, P, u, gphi, lphi, gu, hp, gp, hs, gs);
+            compensate_h<L, C>(hs);
             const long long idx = (long long)zc * nxy + (long long)ys * nx + xs;
             static_for<0, Q>([&](auto I) {
                 constexpr int i = decltype(I)::value;
