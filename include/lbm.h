@@ -209,6 +209,15 @@ int lbm_load_state(lbm_handle h, const void *host_buf, size_t bytes);
  * one FMA differently in different kernels, so variants agree to rounding. */
 int lbm_set_tuning(lbm_handle h, int variant, int zchunk);
 
+/* Testing aid for the failure path of the persistent split step (variant
+ * 4): while set, its moments launch leaves the z-plane `plane` uncounted, so
+ * the collisions that need that plane wait until their bounded wait runs out
+ * (1 s on the GPU's timer); the step then ends, its results are invalid, and
+ * lbm_check / lbm_read_fields report LBM_ERR_TIMEOUT.  The handle stays
+ * usable: clear the aid (plane < 0) and initialise it again.  plane >= nz is
+ * LBM_ERR_INVALID_ARG.  No other variant looks at it. */
+int lbm_debug_stall(lbm_handle h, int plane);
+
 /* Device bytes held by h, and the bytes one step reads and writes at minimum
  * (algorithmic traffic: both population sets in and out, P and u in and out). */
 int lbm_footprint(lbm_handle h, size_t *device_bytes, size_t *step_bytes);

@@ -89,6 +89,7 @@ SIGNATURES = {
     "lbm_reduce_fields_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _i64, ctypes.c_double, ctypes.c_double,
                                                   ctypes.c_int32, _vp, _vp]),
     "lbm_last_error": (ctypes.c_char_p, [_vp]),
+    "lbm_debug_stall": (ctypes.c_int, [_vp, ctypes.c_int]),
     "lbm_estimate_footprint": (ctypes.c_int, [ctypes.POINTER(Grid), ctypes.c_int, ctypes.POINTER(Params),
                                               ctypes.POINTER(ctypes.c_size_t)]),
     "lbm_autotune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -360,6 +361,10 @@ class Lattice:
         """variant 0 auto, 1 fused plane-synchronous, 2 fused pipelined, 3 split form,
         4 persistent split form; zchunk 0 = auto."""
         _check(lib().lbm_set_tuning(self._h, int(variant), int(zchunk)), self._h)
+
+    def debug_stall(self, plane: int):
+        """Testing aid of the persistent step's failure path (see lbm.h)."""
+        _check(lib().lbm_debug_stall(self._h, int(plane)), self._h)
 
     def autotune(self, trial_steps: int = 5):
         """Time every launch form on this lattice's state, keep the fastest,

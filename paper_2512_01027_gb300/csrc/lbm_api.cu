@@ -641,6 +641,14 @@ int lbm_set_tuning(lbm_handle h, int variant, int zchunk)
     return LBM_OK;
 }
 
+int lbm_debug_stall(lbm_handle h, int plane)
+{
+    if (!h) return LBM_ERR_INVALID_ARG;
+    if (plane >= h->nz) return fail(h, LBM_ERR_INVALID_ARG, "plane >= nz");
+    h->persist_stall = plane < 0 ? -1 : plane;
+    return LBM_OK;
+}
+
 int lbm_footprint(lbm_handle h, size_t *device_bytes, size_t *step_bytes)
 {
     if (!h) return LBM_ERR_INVALID_ARG;

@@ -297,6 +297,7 @@ struct Impl {
             p.bpp = (p.nxy + kSplitThreads * kPersistSpan - 1) / (kSplitThreads * kPersistSpan);
             p.zper = L::D == 3 ? c->periodic[2] : 1;
             p.lag = kPersistLag;
+            p.stall = c->persist_stall;
             p.err = c->d_err;
             const long long items = 2LL * p.nz * p.bpp;
             const int g = (int)std::min<long long>(grid, items);

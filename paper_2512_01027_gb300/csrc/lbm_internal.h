@@ -65,6 +65,7 @@ struct lbm_ctx {
     void *fb = nullptr;
     void *pig = nullptr;
     int *pctl = nullptr;           // counters of the persistent split step [2 + nz]
+    int persist_stall = -1;        // testing aid of the persistent step (lbm_debug_stall)
     void *fg[2] = {nullptr, nullptr};   // BF16 storage: odd part V_g of g* per site (float4), follows cur
     bool g_deferred = false;       // the g store holds g* without its odd part, fg[cur] holds V_g
     bool fa_valid = false;         // fa[cur] holds the state

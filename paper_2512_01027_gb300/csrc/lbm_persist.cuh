@@ -34,10 +34,19 @@ struct PersistArgs {
     int nxy;        // sites per plane
     int zper;       // periodic in z
     int lag;        // planes by which the collisions trail the moments (>= 1)
+    int stall;      // testing aid: moments of this plane are not counted (-1: none)
     int *err;       // bit 0 non-finite, bit 1 a dependency wait ran out
 };
 
-constexpr long long kPersistMaxSpin = 1LL << 24;   // >= 1 s of polling
+constexpr long long kPersistMaxSpin = 1LL << 26;            // polls, a backstop to the time limit
+constexpr unsigned long long kPersistWaitNs = 1000000000ull;   // 1 s of waiting per plane
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 constexpr int kPersistLag = 2;
 constexpr int kPersistSpan = 2;   // consecutive 128-site blocks per work item
 
@@ -75,9 +84,10 @@ __device__ __forceinline__ int persist_wait(const PersistArgs &p, int z)
             zz = (zz + p.nz) % p.nz;
         }
         long long it = 0;
+        const unsigned long long t0 = global_ns();
         while (ctl[2 + zz] < p.bpp) {
             if (ctl[1]) return 0;
-            if (++it > kPersistMaxSpin) {
+            if (++it > kPersistMaxSpin || global_ns() - t0 > kPersistWaitNs) {
                 atomicExch(p.ctl + 1, 1);
                 atomicOr(p.err, 2);
                 return 0;
@@ -112,7 +122,7 @@ __global__ void __launch_bounds__(kSplitThreads, kSplitMinBlocks)
             }
             __threadfence();
             __syncthreads();
-            if (threadIdx.x == 0) atomicAdd(p.ctl + 2 + plane, 1);
+            if (threadIdx.x == 0 && plane != p.stall) atomicAdd(p.ctl + 2 + plane, 1);
         } else {
             if (threadIdx.x == 0) s_ok = persist_wait(p, plane);
             __syncthreads();

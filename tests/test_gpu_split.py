@@ -192,6 +192,35 @@ def test_persistent_matches_split(lbm, case, storage, inplace):
                 assert np.abs(x - y).max() <= 1e-2 * max(np.abs(x).max(), 1e-30)
 
 
+def test_persistent_wait_runs_out_and_reports(lbm):
+    """Failure path of the persistent step: with the moments of one plane
+    left uncounted, the collisions that need it wait until their bounded wait
+    (1 s on the GPU timer) runs out; the launch ends, the step reports
+    LBM_ERR_TIMEOUT, and the handle, cleared and initialised again, steps
+    exactly like a fresh one."""
+    import time
+    c = CASES["closed_box_d3q27"]()
+    L = make(lbm, c, "f32", variant=4)
+    L.debug_stall(1)
+    t0 = time.perf_counter()
+    L.step(1)
+    with pytest.raises(lbm.LbmError) as e:
+        L.check()
+    assert e.value.code == lbm.LBM_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    L.debug_stall(-1)
+    L.init_fields(c.phi0, c.P0, c.u0)
+    ref = make(lbm, c, "f32", variant=4)
+    L.step(7)
+    ref.step(7)
+    L.check()
+    for x, y in zip(L.read_fields(), ref.read_fields()):
+        assert np.array_equal(x, y)
+    with pytest.raises(lbm.LbmError) as e:
+        L.debug_stall(10 ** 6)
+    assert e.value.code == lbm.LBM_ERR_INVALID_ARG
+
+
 def test_persistent_refused_for_f64(lbm):
     c = CASES["walls_d3q19"]()
     L = make(lbm, c, "f64")
