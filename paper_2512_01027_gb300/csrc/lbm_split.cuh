@@ -120,50 +120,297 @@ inline constexpr bool kPacked = std::is_same<R, float>::value;
 constexpr int kSplitThreads = 128;
 constexpr int kSplitMinBlocks = 4;   // <= 128 registers a thread: 16 warps an SM
 
-// S0 + S1 at site idx (0 <= idx < a.N).
+// S0 + S1 at site idx with FP32 arithmetic.  Every pulled population and
+// every neighbour word goes straight into running sums, so no per-direction
+// value waits for phi: 1/(T rho) multiplies the pressure sums once, after the
+// loop.  The sums are those of s1_pairs and s1_pressure_pairs (u = sum of the
+// g differences + 1/(T rho) sum w_i c_i {P(x - c_i) - P(x + c_i)} per pair),
+// accumulated as the loads arrive, which leaves registers for more loads in
+// flight.
+template <class L, class C, bool HAS_MASK, int MODE, class IX>
+__device__ __forceinline__ void moments_site_packed(const SplitArgs<float, typename C::S> &a, const int idx,
+                                                    const uint32_t m)
+{
+    constexpr int D = L::D, Q = L::Q;
+    constexpr int NS = D == 3 ? 6 : 3;
+    const IX N = (IX)a.N;
+    const Nbr32 nb(idx, a.nx, a.ny, D == 3 ? a.nz : 1);
+    const float P0 = a.F_old[idx].w;
+    [[maybe_unused]] float vgown[3];
+    if constexpr (C::kGodd) {
+        const float4 v4 = a.G_old[idx];
+        vgown[0] = v4.x; vgown[1] = v4.y; vgown[2] = v4.z;
+    }
+    float phi = 0.f, sumg = 0.f, swP = 0.f, sum_wcu = 0.f;
+    float ug[3] = {0.f, 0.f, 0.f}, up[3] = {0.f, 0.f, 0.f}, pm[NS];
+    static_for<0, NS>([&](auto J) { pm[decltype(J)::value] = 0.f; });
+    float gfirst = 0.f, pfirst = 0.f;   // the first member (c) of the current pair (c, -c)
+    static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const IX e = read_idx<L, MODE, i, IX>(N, nb, idx, m, HAS_MASK);
+        const float hv = C::template dec_h<i>(a.src_h[e]);
+        float gv = C::template dec_g<i>(a.src_g[e]);
+        if constexpr (i == 0) {
+            phi = hv;
+            sumg = gv;
+        } else {
+            phi = phi + hv;
+            const bool bb = HAS_MASK && ((m >> i) & 1u);
+            const int src = nb.at<L, i>(-1);
+            const float4 f = a.F_old[src];
+            const float pn = bb ? P0 : f.w;
+            if constexpr (C::kGodd) {
+                // add back the odd part w_i c_i . V_g of the site the population
+                // left (bounce-back: g*_{-i}(x), whose part is - w_i c_i . V_g(x))
+                const float4 v4 = a.G_old[src];
+                const float vs[3] = {v4.x, v4.y, v4.z};
+                const float corr = bb ? -dot_c<L, i>(vgown) : dot_c<L, i>(vs);
+                gv = gv + float(L::w(i)) * corr;
+            }
+            if (!bb) {
+                const float un[3] = {f.x, f.y, f.z};
+                sum_wcu = sum_wcu + float(L::w(i)) * dot_c<L, i>(un);
+            }
+            if constexpr (i & 1) {
+                gfirst = gv;
+                pfirst = pn;
+            } else {
+                constexpr int ic = i - 1;                    // c_i = -c_ic
+                const float wi = float(L::w(ic));
+                const float dg = gfirst - gv, dp = wi * (pfirst - pn);
+                static_for<0, 3>([&](auto A) {
+                    constexpr int ax = decltype(A)::value;
+                    if constexpr (L::c(ic, ax) != 0) {
+                        acc_c<L::c(ic, ax)>(ug[ax], dg);
+                        acc_c<L::c(ic, ax)>(up[ax], dp);
+                    }
+                });
+                const float gsum = gfirst + gv;
+                sumg = sumg + gsum;
+                swP = swP + wi * (pfirst + pn);
+                // sum_i c_ia c_ib g_i (c_ia c_ib is even in c)
+                static_for<0, D>([&](auto A) {
+                    constexpr int a0 = decltype(A)::value;
+                    static_for<a0, D>([&](auto Bb) {
+                        constexpr int b0 = decltype(Bb)::value;
+                        constexpr int cc = L::c(ic, a0) * L::c(ic, b0);
+                        if constexpr (cc != 0) acc_c<cc>(pm[pig_slot<D>(a0, b0)], gsum);
+                    });
+                });
+            }
+        }
+    });
+    const float phihat = a.k.clamp ? clamp01(phi) : phi;
+    const float rho = a.k.rho_a + phihat * a.k.drho;
+    const float kfac = 3.f / rho;                        // 1 / (T rho)
+    float u[3];
+    static_for<0, 3>([&](auto A) {
+        constexpr int ax = decltype(A)::value;
+        u[ax] = ug[ax] + kfac * up[ax];                  // u = sum_i (g_i + K_i) c_i
+    });
+    const float sumK = kfac * (swP - float(1.0 - L::w(0)) * P0);
+    const float Pnew = s1_pressure_pairs<float, C::kPdev>(a.k, rho, sumg, sumK, sum_wcu, P0);
+    const float uz = D == 3 ? u[2] : 0.f;
+    a.F_new[idx] = make_float4(u[0], u[1], uz, Pnew);
+    a.FB[idx] = make_float4(u[0], u[1], uz, phi);
+    static_for<0, NS>([&](auto J) {
+        constexpr int j = decltype(J)::value;
+        a.PiG[eidx<IX>(j, N, idx)] = pm[j];
+    });
+}
+
+// Separable neighbour sums (D3Q27).  Its weights factor over the axes,
+// w_i = s(c_ix) s(c_iy) s(c_iz) with s(0) = 2/3 and s(+-1) = 1/6, so a
+// weighted sum over the 27 neighbours is three passes of three points: a
+// smoothing S = (1/6, 2/3, 1/6) or a difference D = (-1/6, 0, 1/6) along each
+// axis.  A warp whose 32 sites are consecutive in x and have no solid or
+// outside neighbour does the y and z passes on its own column (9 loads instead
+// of 26) and the x pass across lanes with shuffles; lanes 0 and 31 also
+// take the columns just outside the warp.
+constexpr float kS0 = 2.f / 3.f, kS1 = 1.f / 6.f;
+
+__device__ __forceinline__ float sm3(float m, float c, float p) { return kS1 * (m + p) + kS0 * c; }
+__device__ __forceinline__ float df3(float m, float p) { return kS1 * (p - m); }
+
+// y and z passes over the packed (u, P) words of one column, rows r[1 + dy][1 + dz]:
+// sP = S_y S_z P, dyP = D_y S_z P, dzP = S_y D_z P, sUx = S_y S_z u_x,
+// e = D_y S_z u_y + S_y D_z u_z.
+struct ColUP {
+    float sP, dyP, dzP, sUx, e;
+};
+
+__device__ __forceinline__ ColUP col_up(const float4 (&r)[3][3])
+{
+    float szP[3], dzP[3], szUx[3], szUy[3], dzUz[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        szP[j] = sm3(r[j][0].w, r[j][1].w, r[j][2].w);
+        dzP[j] = df3(r[j][0].w, r[j][2].w);
+        szUx[j] = sm3(r[j][0].x, r[j][1].x, r[j][2].x);
+        szUy[j] = sm3(r[j][0].y, r[j][1].y, r[j][2].y);
+        dzUz[j] = df3(r[j][0].z, r[j][2].z);
+    }
+    ColUP o;
+    o.sP = sm3(szP[0], szP[1], szP[2]);
+    o.dyP = df3(szP[0], szP[2]);
+    o.dzP = sm3(dzP[0], dzP[1], dzP[2]);
+    o.sUx = sm3(szUx[0], szUx[1], szUx[2]);
+    o.e = df3(szUy[0], szUy[2]) + sm3(dzUz[0], dzUz[1], dzUz[2]);
+    return o;
+}
+
+template <bool CG>
+__device__ __forceinline__ void load_col(const float4 *F, int xo, const Nbr32 &nb, float4 (&r)[3][3])
+{
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if constexpr (CG) r[j][k] = __ldcg(F + xo + nb.yo[j] + nb.zo[k]);
+            else r[j][k] = F[xo + nb.yo[j] + nb.zo[k]];
+        }
+}
+
+// Value of the lane at x - 1 (lane 0: h, the column before the warp) and at x + 1.
+__device__ __forceinline__ float lane_xm(float v, float h, int lane)
+{
+    const float t = __shfl_up_sync(0xffffffffu, v, 1);
+    return lane == 0 ? h : t;
+}
+__device__ __forceinline__ float lane_xp(float v, float h, int lane)
+{
+    const float t = __shfl_down_sync(0xffffffffu, v, 1);
+    return lane == 31 ? h : t;
+}
+
+// S0 + S1 at site idx, separable form (D3Q27, FP32 arithmetic, a warp of 32
+// sites in one row, none with a solid or outside neighbour; every lane of the
+// warp calls it).  With no bounce-back every sum runs over all 26 neighbours:
+//   sum_i w_i P(x - c_i)         = S_x S_y S_z P
+//   sum_i w_i c_ia P(x - c_i)    = - D_a S S P
+//   sum_i w_i c_i . u(x - c_i)   = - sum_a D_a S S u_a
+// the same quantities moments_site_packed sums direction by direction.
+template <class L, class C, int MODE, class IX>
+__device__ __forceinline__ void moments_site_sep(const SplitArgs<float, typename C::S> &a, const int idx)
+{
+    static_assert(L::Q == 27 && !C::kGodd, "separable moments: D3Q27 without the odd-part deferral");
+    constexpr int Q = L::Q, NS = 6;
+    const IX N = (IX)a.N;
+    const Nbr32 nb(idx, a.nx, a.ny, a.nz);
+    const int lane = (int)(threadIdx.x & 31u);
+    float4 r[3][3];
+    load_col<false>(a.F_old, nb.xo[1], nb, r);
+    const float P0 = r[1][1].w;
+    float phi = 0.f, sumg = 0.f;
+    float ug[3] = {0.f, 0.f, 0.f}, pm[NS];
+    static_for<0, NS>([&](auto J) { pm[decltype(J)::value] = 0.f; });
+    float gfirst = 0.f;
+    static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const IX e = read_idx<L, MODE, i, IX>(N, nb, idx, 0u, false);
+        const float hv = C::template dec_h<i>(a.src_h[e]);
+        const float gv = C::template dec_g<i>(a.src_g[e]);
+        if constexpr (i == 0) {
+            phi = hv;
+            sumg = gv;
+        } else {
+            phi = phi + hv;
+            if constexpr (i & 1) {
+                gfirst = gv;
+            } else {
+                constexpr int ic = i - 1;
+                const float dg = gfirst - gv;
+                static_for<0, 3>([&](auto A) {
+                    constexpr int ax = decltype(A)::value;
+                    if constexpr (L::c(ic, ax) != 0) acc_c<L::c(ic, ax)>(ug[ax], dg);
+                });
+                const float gsum = gfirst + gv;
+                sumg = sumg + gsum;
+                static_for<0, 3>([&](auto A) {
+                    constexpr int a0 = decltype(A)::value;
+                    static_for<a0, 3>([&](auto Bb) {
+                        constexpr int b0 = decltype(Bb)::value;
+                        constexpr int cc = L::c(ic, a0) * L::c(ic, b0);
+                        if constexpr (cc != 0) acc_c<cc>(pm[pig_slot<3>(a0, b0)], gsum);
+                    });
+                });
+            }
+        }
+    });
+    const ColUP own = col_up(r);
+    ColUP hal = own;
+    if (lane == 0 || lane == 31) {
+        float4 rh[3][3];
+        load_col<false>(a.F_old, lane == 0 ? nb.xo[0] : nb.xo[2], nb, rh);
+        hal = col_up(rh);
+    }
+    const float sPm = lane_xm(own.sP, hal.sP, lane), sPp = lane_xp(own.sP, hal.sP, lane);
+    const float sssP = sm3(sPm, own.sP, sPp);
+    float up[3];
+    up[0] = -df3(sPm, sPp);
+    up[1] = -sm3(lane_xm(own.dyP, hal.dyP, lane), own.dyP, lane_xp(own.dyP, hal.dyP, lane));
+    up[2] = -sm3(lane_xm(own.dzP, hal.dzP, lane), own.dzP, lane_xp(own.dzP, hal.dzP, lane));
+    const float divu = df3(lane_xm(own.sUx, hal.sUx, lane), lane_xp(own.sUx, hal.sUx, lane)) +
+                       sm3(lane_xm(own.e, hal.e, lane), own.e, lane_xp(own.e, hal.e, lane));
+    const float sum_wcu = -divu;
+    const float swP = sssP - float(L::w(0)) * P0;
+    const float phihat = a.k.clamp ? clamp01(phi) : phi;
+    const float rho = a.k.rho_a + phihat * a.k.drho;
+    const float kfac = 3.f / rho;
+    float u[3];
+    static_for<0, 3>([&](auto A) {
+        constexpr int ax = decltype(A)::value;
+        u[ax] = ug[ax] + kfac * up[ax];
+    });
+    const float sumK = kfac * (swP - float(1.0 - L::w(0)) * P0);
+    const float Pnew = s1_pressure_pairs<float, C::kPdev>(a.k, rho, sumg, sumK, sum_wcu, P0);
+    a.F_new[idx] = make_float4(u[0], u[1], u[2], Pnew);
+    a.FB[idx] = make_float4(u[0], u[1], u[2], phi);
+    static_for<0, NS>([&](auto J) {
+        constexpr int j = decltype(J)::value;
+        a.PiG[eidx<IX>(j, N, idx)] = pm[j];
+    });
+}
+
+// True when the separable form applies to this kernel instantiation.
+template <class L, class R, class C>
+inline constexpr bool kSepForm = kPacked<R> && L::Q == 27 && !C::kGodd;
+
+// S0 + S1 at site idx (0 <= idx < a.N).  FP64: the canonical order of the
+// oracle; FP32 arithmetic: moments_site_packed.
 template <class L, class R, class C, bool HAS_MASK, int MODE, class IX>
 __device__ __forceinline__ void moments_site(const SplitArgs<R, typename C::S> &a, const int idx)
 {
     constexpr int D = L::D, Q = L::Q;
     uint32_t m = 0;
     if constexpr (HAS_MASK) m = a.mask[idx];
-    if (m & kSolidBit) return;
-    const IX N = (IX)a.N;
-    const Nbr32 nb(idx, a.nx, a.ny, D == 3 ? a.nz : 1);
-    R hp[Q], gp[Q], Pn[Q], K[Q];
-    R P0;
-    if constexpr (kPacked<R>) P0 = a.F_old[idx].w;
-    else P0 = a.P_old[idx];
-    R sum_wcu = R(0);
-    [[maybe_unused]] float vgown[3];
-    if constexpr (kPacked<R> && C::kGodd) {
-        const float4 v4 = a.G_old[idx];
-        vgown[0] = v4.x; vgown[1] = v4.y; vgown[2] = v4.z;
+    if constexpr (kSepForm<L, R, C>) {
+        // nx a multiple of 32: every warp is 32 consecutive sites of one row
+        if ((a.nx & 31) == 0 && !(HAS_MASK && __any_sync(0xffffffffu, m != 0u))) {
+            moments_site_sep<L, C, MODE, IX>(a, idx);
+            return;
+        }
     }
-    static_for<0, Q>([&](auto I) {
-        constexpr int i = decltype(I)::value;
-        const IX e = read_idx<L, MODE, i, IX>(N, nb, idx, m, HAS_MASK);
-        hp[i] = C::template dec_h<i>(a.src_h[e]);
-        gp[i] = C::template dec_g<i>(a.src_g[e]);
-        if constexpr (i == 0) {
-            Pn[0] = P0;
-        } else {
-            const bool bb = HAS_MASK && ((m >> i) & 1u);
-            const int src = nb.at<L, i>(-1);
-            R un[3];
-            if constexpr (kPacked<R>) {
-                const float4 f = a.F_old[src];
-                Pn[i] = bb ? P0 : f.w;
-                un[0] = f.x; un[1] = f.y; un[2] = f.z;
-                if constexpr (C::kGodd) {
-                    // add back the odd part w_i c_i . V_g of the site the population
-                    // left (bounce-back: g*_{-i}(x), whose part is - w_i c_i . V_g(x))
-                    const float4 v4 = a.G_old[src];
-                    const float vs[3] = {v4.x, v4.y, v4.z};
-                    const float corr = bb ? -dot_c<L, i>(vgown) : dot_c<L, i>(vs);
-                    gp[i] = gp[i] + float(L::w(i)) * corr;
-                }
+    if (m & kSolidBit) return;
+    if constexpr (kPacked<R>) {
+        moments_site_packed<L, C, HAS_MASK, MODE, IX>(a, idx, m);
+    } else {
+        const IX N = (IX)a.N;
+        const Nbr32 nb(idx, a.nx, a.ny, D == 3 ? a.nz : 1);
+        R hp[Q], gp[Q], Pn[Q], K[Q];
+        const R P0 = a.P_old[idx];
+        R sum_wcu = R(0);
+        static_for<0, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            const IX e = read_idx<L, MODE, i, IX>(N, nb, idx, m, HAS_MASK);
+            hp[i] = C::template dec_h<i>(a.src_h[e]);
+            gp[i] = C::template dec_g<i>(a.src_g[e]);
+            if constexpr (i == 0) {
+                Pn[0] = P0;
             } else {
+                const bool bb = HAS_MASK && ((m >> i) & 1u);
+                const int src = nb.at<L, i>(-1);
+                R un[3];
                 Pn[i] = bb ? P0 : a.P_old[src];
                 static_for<0, 3>([&](auto A) {
                     constexpr int ax = decltype(A)::value;
@@ -173,44 +420,12 @@ __device__ __forceinline__ void moments_site(const SplitArgs<R, typename C::S> &
                         un[ax] = R(0);
                     }
                 });
+                if (!bb) sum_wcu = sum_wcu + R(L::w(i)) * dot_c<L, i>(un);
             }
-            if (!bb) sum_wcu = sum_wcu + R(L::w(i)) * dot_c<L, i>(un);
-        }
-    });
-    R phi, phihat, rho, u[3], sumg, sumK;
-    R Pnew;
-    if constexpr (kPairForms<R>) {
-        s1_pairs<L, R>(a.k, hp, gp, Pn, P0, phi, phihat, rho, u, sumg, sumK);
-        Pnew = s1_pressure_pairs<R, C::kPdev>(a.k, rho, sumg, sumK, sum_wcu, P0);
-    } else {
+        });
+        R phi, phihat, rho, u[3];
         s1_moments<L, R>(a.k, hp, gp, Pn, P0, phi, phihat, rho, u, K);
-        Pnew = s1_pressure<L, R, C::kPdev>(a.k, gp, K, rho, sum_wcu, P0);
-    }
-    if constexpr (kPacked<R>) {
-        const float uz = D == 3 ? u[2] : 0.f;
-        a.F_new[idx] = make_float4(u[0], u[1], uz, Pnew);
-        a.FB[idx] = make_float4(u[0], u[1], uz, phi);
-        // sum_i c_ia c_ib g_i, per pair (c_ia c_ib is even in c)
-        constexpr int NS = D == 3 ? 6 : 3;
-        float pm[NS];
-        static_for<0, NS>([&](auto J) { pm[decltype(J)::value] = 0.f; });
-        static_for<0, (Q - 1) / 2>([&](auto Pp) {
-            constexpr int i = 2 * decltype(Pp)::value + 1;
-            const float gsum = gp[i] + gp[i + 1];
-            static_for<0, D>([&](auto A) {
-                constexpr int a0 = decltype(A)::value;
-                static_for<a0, D>([&](auto Bb) {
-                    constexpr int b0 = decltype(Bb)::value;
-                    constexpr int cc = L::c(i, a0) * L::c(i, b0);
-                    if constexpr (cc != 0) acc_c<cc>(pm[pig_slot<D>(a0, b0)], gsum);
-                });
-            });
-        });
-        static_for<0, NS>([&](auto J) {
-            constexpr int j = decltype(J)::value;
-            a.PiG[eidx<IX>(j, N, idx)] = pm[j];
-        });
-    } else {
+        const R Pnew = s1_pressure<L, R, C::kPdev>(a.k, gp, K, rho, sum_wcu, P0);
         a.P_new[idx] = Pnew;
         static_for<0, D>([&](auto A) {
             constexpr int ax = decltype(A)::value;

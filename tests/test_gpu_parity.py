@@ -192,6 +192,36 @@ def test_short_horizon_f32(lbm, lat):
     assert np.abs(f1 - f2).max() <= 1e-5
 
 
+def _wide_3d(geom):
+    """D3Q27 boxes whose rows are whole warps (nx a multiple of 32)."""
+    if geom == "periodic":
+        return small_3d("D3Q27", nx=32, ny=6, nz=8, walls=False)
+    c = small_3d("D3Q27", nx=64, ny=7, nz=9, walls=True)
+    if geom == "walls_block":
+        # a solid block: warps next to it take the direction-by-direction sums
+        c.solid[3:6, 2:5, 40:47] = 1
+        c.phi0 = np.where(c.solid.astype(bool), 0.0, c.phi0)
+        c.u0[:, c.solid.astype(bool)] = 0
+    return c
+
+
+@pytest.mark.parametrize("geom", ["walls", "walls_block", "periodic"])
+@pytest.mark.parametrize("variant", [0, 4])
+def test_separable_sums_f32_short_horizon(lbm, geom, variant):
+    """A warp of 32 sites in one row with no solid or outside neighbour sums
+    its neighbours in separable form (the D3Q27 weights factor over the
+    axes); the other warps sum direction by direction.  Both against the
+    oracle at the short-horizon FP32 bounds, for the split form and the
+    persistent split step."""
+    c = _wide_3d(geom)
+    _, g = run_gpu(lbm, c, 5, storage="f32", variant=variant)
+    _, o = run_oracle(c, 5)
+    (f1, P1, u1), (f2, P2, u2) = g, o
+    assert np.abs(u1 - u2).max() <= 1e-5 * np.abs(u2).max()
+    assert np.abs(P1 - P2).max() <= 5e-5 * c.params["sigma"] / 4.0
+    assert np.abs(f1 - f2).max() <= 1e-5
+
+
 @pytest.mark.parametrize("storage,tol", [("f64", 1e-12), ("f32", 1e-4), ("f16", 1e-2), ("bf16", 1e-2)])
 def test_laplace_pressure_long_run(lbm, storage, tol):
     """64^2 droplet, 10000 steps: the Laplace jump dP = P_in - P_out of the

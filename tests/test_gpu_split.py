@@ -44,6 +44,7 @@ CASES = {
     "walls_d3q19": lambda: small_3d("D3Q19"),
     "closed_box_d3q27": lambda: closed_box_3d("D3Q27"),
     "periodic_thin_d3q27": lambda: small_3d("D3Q27", nx=9, ny=7, nz=5, walls=False),
+    "wide_walls_d3q27": lambda: small_3d("D3Q27", nx=64, ny=5, nz=7),
 }
 
 
