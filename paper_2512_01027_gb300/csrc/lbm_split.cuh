@@ -259,16 +259,12 @@ __device__ __forceinline__ ColUP col_up(const float4 (&r)[3][3])
     return o;
 }
 
-template <bool CG>
 __device__ __forceinline__ void load_col(const float4 *F, int xo, const Nbr32 &nb, float4 (&r)[3][3])
 {
 #pragma unroll
     for (int j = 0; j < 3; ++j)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            if constexpr (CG) r[j][k] = __ldcg(F + xo + nb.yo[j] + nb.zo[k]);
-            else r[j][k] = F[xo + nb.yo[j] + nb.zo[k]];
-        }
+        for (int k = 0; k < 3; ++k) r[j][k] = F[xo + nb.yo[j] + nb.zo[k]];
 }
 
 // Column whose sums lane 0 (x - 1) and lane 31 (x + 1) need from outside the
@@ -307,8 +303,8 @@ __device__ __forceinline__ void moments_site_sep(const SplitArgs<float, typename
     const Nbr32 nb(idx, a.nx, a.ny, a.nz);
     const int lane = (int)(threadIdx.x & 31u);
     float4 r[3][3], rh[3][3];
-    load_col<false>(a.F_old, nb.xo[1], nb, r);
-    load_col<false>(a.F_old, halo_col(nb, lane), nb, rh);
+    load_col(a.F_old, nb.xo[1], nb, r);
+    load_col(a.F_old, halo_col(nb, lane), nb, rh);
     const float P0 = r[1][1].w;
     float phi = 0.f, sumg = 0.f;
     float ug[3] = {0.f, 0.f, 0.f}, pm[NS];
@@ -376,72 +372,10 @@ __device__ __forceinline__ void moments_site_sep(const SplitArgs<float, typename
     });
 }
 
-// True when the separable form applies to this kernel instantiation (the
-// moments launch; its BF16 odd-part corrections are per direction).
+// True when the separable form applies to this kernel instantiation (its
+// BF16 odd-part corrections are per direction).
 template <class L, class R, class C>
 inline constexpr bool kSepForm = kPacked<R> && L::Q == 27 && !C::kGodd;
-
-// y and z passes over the packed (u, phi) words of one column, per field
-// f = u_x, u_y, u_z, phi: s = S_y S_z f, dy = D_y S_z f, dz = S_y D_z f.
-struct ColFB {
-    float s[4], dy[4], dz[4];
-};
-
-__device__ __forceinline__ float fb_comp(const float4 &v, int f)
-{
-    return f == 0 ? v.x : (f == 1 ? v.y : (f == 2 ? v.z : v.w));
-}
-
-__device__ __forceinline__ ColFB col_fb(const float4 (&r)[3][3])
-{
-    ColFB o;
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-        float sz[3], dz[3];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            sz[j] = sm3(fb_comp(r[j][0], f), fb_comp(r[j][1], f), fb_comp(r[j][2], f));
-            dz[j] = df3(fb_comp(r[j][0], f), fb_comp(r[j][2], f));
-        }
-        o.s[f] = sm3(sz[0], sz[1], sz[2]);
-        o.dy[f] = df3(sz[0], sz[2]);
-        o.dz[f] = sm3(dz[0], dz[1], dz[2]);
-    }
-    return o;
-}
-
-// Stencils of the collision launch in separable form (same conditions as
-// moments_site_sep; every lane of the warp calls it):
-//   grad f = (1/T) sum_i w_i c_i f(x + c_i)            = 3 (D_x S S, S D_y S, S S D_z) f
-//   lap phi = (2/T) sum_i w_i {phi(x + c_i) - phi(x)}  = 6 (S S S phi - phi)
-template <bool CG>
-__device__ __forceinline__ void stencil_sep(const float4 *FB, const Nbr32 &nb, float phi0, float (&gphi)[3],
-                                            float &lphi, float (&gu)[3][3])
-{
-    const int lane = (int)(threadIdx.x & 31u);
-    float4 r[3][3], rh[3][3];
-    load_col<CG>(FB, nb.xo[1], nb, r);
-    load_col<CG>(FB, halo_col(nb, lane), nb, rh);
-    const ColFB own = col_fb(r);
-    const ColFB hal = col_fb(rh);
-#pragma unroll
-    for (int f = 0; f < 4; ++f) {
-        const float sm = lane_xm(own.s[f], hal.s[f], lane), sp = lane_xp(own.s[f], hal.s[f], lane);
-        const float gx = df3(sm, sp);
-        const float gy = sm3(lane_xm(own.dy[f], hal.dy[f], lane), own.dy[f], lane_xp(own.dy[f], hal.dy[f], lane));
-        const float gz = sm3(lane_xm(own.dz[f], hal.dz[f], lane), own.dz[f], lane_xp(own.dz[f], hal.dz[f], lane));
-        if (f < 3) {
-            gu[f][0] = 3.f * gx;
-            gu[f][1] = 3.f * gy;
-            gu[f][2] = 3.f * gz;
-        } else {
-            gphi[0] = 3.f * gx;
-            gphi[1] = 3.f * gy;
-            gphi[2] = 3.f * gz;
-            lphi = (sm3(sm, own.s[3], sp) - phi0) * 6.f;
-        }
-    }
-}
 
 // S0 + S1 at site idx (0 <= idx < a.N).  FP64: the canonical order of the
 // oracle; FP32 arithmetic: moments_site_packed.
@@ -518,10 +452,6 @@ __device__ __forceinline__ void collide_site(const SplitArgs<R, typename C::S> &
     constexpr int D = L::D, Q = L::Q;
     uint32_t m = 0;
     if constexpr (HAS_MASK) m = a.mask[idx];
-    // separable stencils for warps of one row without solid or outside neighbours
-    bool sep = false;
-    if constexpr (kPacked<R> && L::Q == 27)
-        sep = (a.nx & 31) == 0 && !(HAS_MASK && __any_sync(0xffffffffu, m != 0u));
     if (m & kSolidBit) return;
     const IX N = (IX)a.N;
     const Nbr32 nb(idx, a.nx, a.ny, D == 3 ? a.nz : 1);
@@ -529,14 +459,28 @@ __device__ __forceinline__ void collide_site(const SplitArgs<R, typename C::S> &
     R phi, gphi[3], lphi;
     R u[3], gu[3][3];
     R P;
+    constexpr int NS = D == 3 ? 6 : 3;
+    [[maybe_unused]] typename C::S hraw[Q];
+    [[maybe_unused]] float pm[NS];
     if constexpr (kPacked<R>) {
+        // the pulled h and the second moments of g are issued before the
+        // stencil's loads (a compiler-only fence keeps that order), so that a
+        // thread has all its loads in flight at once
+        static_for<0, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            hraw[i] = a.src_h[read_idx<L, MODE, i, IX>(N, nb, idx, m, HAS_MASK)];
+        });
+        static_for<0, NS>([&](auto J) {
+            constexpr int j = decltype(J)::value;
+            pm[j] = ld_maybe_cg<CG>(a.PiG + eidx<IX>(j, N, idx));
+        });
+        asm volatile("" ::: "memory");
         const float4 f0 = ld_maybe_cg<CG>(a.FB + idx);
         u[0] = f0.x; u[1] = f0.y; u[2] = f0.z;
         phi = f0.w;
         P = ld_maybe_cg<CG>(a.F_new + idx).w;
         auto at = [&](auto I, int s) { return ld_maybe_cg<CG>(a.FB + nb.at<L, decltype(I)::value>(s)); };
-        if (sep) stencil_sep<CG>(a.FB, nb, phi, gphi, lphi, gu);
-        else if (m == 0u) stencil_packed<L, false>(at, m, phi, gphi, lphi, gu);
+        if (m == 0u) stencil_packed<L, false>(at, m, phi, gphi, lphi, gu);
         else stencil_packed<L, true>(at, m, phi, gphi, lphi, gu);
     } else {
         P = a.P_new[idx];
@@ -560,13 +504,7 @@ __device__ __forceinline__ void collide_site(const SplitArgs<R, typename C::S> &
     if constexpr (kPacked<R>) {
         static_for<0, Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
-            hp[i] = C::template dec_h<i>(a.src_h[read_idx<L, MODE, i, IX>(N, nb, idx, m, HAS_MASK)]);
-        });
-        constexpr int NS = D == 3 ? 6 : 3;
-        float pm[NS];
-        static_for<0, NS>([&](auto J) {
-            constexpr int j = decltype(J)::value;
-            pm[j] = ld_maybe_cg<CG>(a.PiG + eidx<IX>(j, N, idx));
+            hp[i] = C::template dec_h<i>(hraw[i]);
         });
         float vg[3];
         collide_pairs<L, false, C::kPdev, true, C::kGodd>(a.k, phi, phihat, rho, P, u, gphi, lphi, gu, hp, nullptr,

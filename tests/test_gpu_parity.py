@@ -208,11 +208,11 @@ def _wide_3d(geom):
 @pytest.mark.parametrize("geom", ["walls", "walls_block", "periodic"])
 @pytest.mark.parametrize("variant", [0, 4])
 def test_separable_sums_f32_short_horizon(lbm, geom, variant):
-    """A warp of 32 sites in one row with no solid or outside neighbour sums
-    its neighbours in separable form (the D3Q27 weights factor over the
-    axes); the other warps sum direction by direction.  Both against the
-    oracle at the short-horizon FP32 bounds, for the split form and the
-    persistent split step."""
+    """In the moments launch a warp of 32 sites in one row with no solid or
+    outside neighbour sums its neighbours' (u, P) in separable form (the
+    D3Q27 weights factor over the axes); the other warps sum direction by
+    direction.  Both against the oracle at the short-horizon FP32 bounds, for
+    the split form and the persistent split step."""
     c = _wide_3d(geom)
     _, g = run_gpu(lbm, c, 5, storage="f32", variant=variant)
     _, o = run_oracle(c, 5)
