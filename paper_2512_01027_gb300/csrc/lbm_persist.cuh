@@ -73,19 +73,33 @@ __device__ __forceinline__ void persist_unit(int u, int nz, int lag, int &phase,
 }
 
 // Wait until the moments of planes z-1, z, z+1 are complete.  Returns 0 if
-// the wait was abandoned (timeout here or elsewhere).
+// the wait was abandoned (timeout here or elsewhere).  The three counters are
+// read together first: usually they are already complete.
 __device__ __forceinline__ int persist_wait(const PersistArgs &p, int z)
 {
     volatile int *ctl = p.ctl;
-    for (int dz = -1; dz <= 1; ++dz) {
-        int zz = z + dz;
-        if (zz < 0 || zz >= p.nz) {
-            if (!p.zper) continue;
-            zz = (zz + p.nz) % p.nz;
+    int zz[3];
+    bool need[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        zz[k] = z + k - 1;
+        need[k] = true;
+        if (zz[k] < 0 || zz[k] >= p.nz) {
+            need[k] = p.zper != 0;
+            zz[k] = (zz[k] + p.nz) % p.nz;
         }
+    }
+    const int c0 = ctl[2 + zz[0]], c1 = ctl[2 + zz[1]], c2 = ctl[2 + zz[2]];
+    if ((!need[0] || c0 >= p.bpp) && c1 >= p.bpp && (!need[2] || c2 >= p.bpp)) {
+        __threadfence();
+        return 1;
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (!need[k]) continue;
         long long it = 0;
         const unsigned long long t0 = global_ns();
-        while (ctl[2 + zz] < p.bpp) {
+        while (ctl[2 + zz[k]] < p.bpp) {
             if (ctl[1]) return 0;
             if (++it > kPersistMaxSpin || global_ns() - t0 > kPersistWaitNs) {
                 atomicExch(p.ctl + 1, 1);

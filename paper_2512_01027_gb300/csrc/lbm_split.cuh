@@ -462,10 +462,13 @@ __device__ __forceinline__ void collide_site(const SplitArgs<R, typename C::S> &
     constexpr int NS = D == 3 ? 6 : 3;
     [[maybe_unused]] typename C::S hraw[Q];
     [[maybe_unused]] float pm[NS];
-    if constexpr (kPacked<R>) {
-        // the pulled h and the second moments of g are issued before the
-        // stencil's loads (a compiler-only fence keeps that order), so that a
-        // thread has all its loads in flight at once
+    // 4-byte storage, ping-pong store: the pulled h and the second moments of
+    // g are issued before the stencil's loads (a compiler-only fence keeps
+    // that order), so that a thread has its loads in flight together.  With
+    // 16-bit storage (decoding) and in the in-place store (its index
+    // selections) the registers do not allow it: there they follow the stencil.
+    constexpr bool kEarlyH = kPacked<R> && sizeof(typename C::S) == 4 && MODE == kPingPong;
+    auto load_h_pig = [&]() {
         static_for<0, Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
             hraw[i] = a.src_h[read_idx<L, MODE, i, IX>(N, nb, idx, m, HAS_MASK)];
@@ -474,7 +477,12 @@ __device__ __forceinline__ void collide_site(const SplitArgs<R, typename C::S> &
             constexpr int j = decltype(J)::value;
             pm[j] = ld_maybe_cg<CG>(a.PiG + eidx<IX>(j, N, idx));
         });
-        asm volatile("" ::: "memory");
+    };
+    if constexpr (kPacked<R>) {
+        if constexpr (kEarlyH) {
+            load_h_pig();
+            asm volatile("" ::: "memory");
+        }
         const float4 f0 = ld_maybe_cg<CG>(a.FB + idx);
         u[0] = f0.x; u[1] = f0.y; u[2] = f0.z;
         phi = f0.w;
@@ -502,6 +510,7 @@ __device__ __forceinline__ void collide_site(const SplitArgs<R, typename C::S> &
     const R rho = a.k.rho_a + phihat * a.k.drho;
     R hp[Q], hs[Q], gs[Q];
     if constexpr (kPacked<R>) {
+        if constexpr (!kEarlyH) load_h_pig();
         static_for<0, Q>([&](auto I) {
             constexpr int i = decltype(I)::value;
             hp[i] = C::template dec_h<i>(hraw[i]);
