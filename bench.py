@@ -61,10 +61,16 @@ def parse():
 
 
 def kernel_source_hash() -> str:
+    """Hash of what the step kernels are compiled from: the device headers,
+    the instantiation units and the build flags (host-only API code is left
+    out, it does not change the kernels' traffic)."""
     h = hashlib.sha256()
-    for f in sorted(os.listdir(CSRC)):
-        with open(os.path.join(CSRC, f), "rb") as fh:
-            h.update(f.encode())
+    files = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC))
+             if f.endswith((".cuh", ".h")) or f.startswith("lbm_inst_")]
+    files.append(os.path.join(CSRC, "..", "build.py"))
+    for path in files:
+        with open(path, "rb") as fh:
+            h.update(os.path.basename(path).encode())
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -298,20 +304,24 @@ def run_ours(args):
         dptr = ctypes.POINTER(ctypes.c_double)
         cast = lambda t: ctypes.cast(t.data_ptr(), dptr)  # noqa: E731
         lib = lbm.lib()
+        solves = 3
         torch.cuda.synchronize()
         barrier(world)
         t0 = time.perf_counter()
-        rc = lib.lbm_init_fields(L.handle, cast(phi_h), cast(P_h), cast(u_h))
-        rc |= lib.lbm_step(L.handle, ke)
-        rc |= lib.lbm_read_fields(L.handle, cast(out_phi), cast(out_P), cast(out_u))
+        rc = 0
+        for _ in range(solves):
+            rc |= lib.lbm_init_fields(L.handle, cast(phi_h), cast(P_h), cast(u_h))
+            rc |= lib.lbm_step(L.handle, ke)
+            rc |= lib.lbm_read_fields(L.handle, cast(out_phi), cast(out_P), cast(out_u))
         t_e2e = time.perf_counter() - t0
         barrier(world)
         if rc != 0:
             raise RuntimeError(lib.lbm_last_error(L.handle))
         t_e2e = reduce_max(t_e2e, world)
-        e2e = {"value": N * ke * world / t_e2e / 1e6, "unit": UNIT,
+        e2e = {"value": N * ke * solves * world / t_e2e / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": int(5 * 8 * N / ke), "d2h_bytes_per_step": int(5 * 8 * N / ke),
-               "solve": f"init_fields from pinned host fields, {ke} steps, read_fields to pinned host"}
+               "solve": f"{solves} solves back to back, each init_fields from pinned host fields, "
+                        f"{ke} steps, read_fields to pinned host"}
 
     state_gb = L.footprint()[0] / 1e9
     serve = None

@@ -131,7 +131,17 @@ int lbm_set_allocator(lbm_alloc_fn alloc, lbm_free_fn free_fn, void *ctx);
 /* Initial state from host fields phi[N], P[N], u[3][N]: populations start at
  * equilibrium (Sec. I: "f_i in the initial condition is assumed to be the
  * equilibrium state"), h* = h_eq, g* = g_eq built from these fields and their
- * stencils; P^0 = P, u^0 = u.  Resets the step counter. */
+ * stencils; P^0 = P, u^0 = u.  Resets the step counter.  Returns after the
+ * host arrays have been read (the caller may reuse them).
+ *
+ * Staging of the host-array calls (lbm_init_fields, lbm_read_fields,
+ * lbm_get_state, lbm_probe): the data pass through a device buffer.  With no
+ * allocator hook it comes from one stream-ordered memory pool per device that
+ * keeps its memory for later calls of any handle on that device: it holds the
+ * largest staging size used so far (40 B per site for the fields, 16 Q + 32 B
+ * per site for lbm_get_state) until the process exits.  With a hook
+ * (lbm_set_allocator) it comes from the hook and is released before the call
+ * returns.  Neither is counted by lbm_footprint. */
 int lbm_init_fields(lbm_handle h, const double *phi, const double *P, const double *u);
 
 /* Same from device arrays (double, same layout) already on the handle's device. */

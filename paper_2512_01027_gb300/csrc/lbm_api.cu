@@ -169,14 +169,61 @@ int sync_and_check(lbm_ctx *c)
     return LBM_OK;
 }
 
-// temporary device buffer released at scope exit (after the stream drains)
+// Staging memory of the host-field calls: one stream-ordered pool per device
+// that keeps what it has allocated (release threshold unbounded), so a call
+// reuses the previous call's memory instead of paying a cudaMalloc and a
+// synchronising cudaFree of the fields' size.  Held: the largest staging area
+// used so far on the device (40 B per site of the largest lattice).
+cudaMemPool_t staging_pool(int dev)
+{
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!pools[dev]) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool = nullptr;
+        if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        pools[dev] = pool;
+    }
+    return pools[dev];
+}
+
+// Temporary device buffer of one call: from the staging pool, freed in
+// stream order at scope exit; with an allocator hook set, from the hook,
+// released after the stream drains.
 struct Temp {
     lbm_ctx *c;
     void *p = nullptr;
-    Temp(lbm_ctx *ctx, size_t bytes) : c(ctx) { p = dev_alloc(c, bytes); }
+    bool pooled = false;
+    Temp(lbm_ctx *ctx, size_t bytes) : c(ctx)
+    {
+        if (!c->allocator.alloc) {
+            cudaMemPool_t pool = staging_pool(c->device);
+            if (pool && cudaMallocFromPoolAsync(&p, bytes, pool, c->stream) == cudaSuccess) {
+                pooled = true;
+                return;
+            }
+            cudaGetLastError();
+            p = nullptr;
+        }
+        p = dev_alloc(c, bytes);
+    }
     ~Temp()
     {
-        if (p) {
+        if (!p) return;
+        if (pooled) {
+            cudaFreeAsync(p, c->stream);
+        } else {
             cudaStreamSynchronize(c->stream);
             dev_free(c, p);
         }
@@ -432,6 +479,8 @@ int lbm_init_fields(lbm_handle h, const double *phi, const double *P, const doub
     if (rc == LBM_OK) rc = cuda_fail(h, cudaMemcpyAsync(d + n, P, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream), "H2D P");
     if (rc == LBM_OK) rc = cuda_fail(h, cudaMemcpyAsync(d + 2 * n, u, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, h->stream), "H2D u");
     if (rc == LBM_OK) rc = lbm_init_fields_device(h, d, d + n, d + 2 * n);
+    // the caller may reuse phi, P, u as soon as this returns
+    if (rc == LBM_OK) rc = cuda_fail(h, cudaStreamSynchronize(h->stream), "cudaStreamSynchronize");
     return rc;
 }
 
