@@ -385,10 +385,13 @@ __device__ __forceinline__ void moments_site(const SplitArgs<R, typename C::S> &
     constexpr int D = L::D, Q = L::Q;
     uint32_t m = 0;
     if constexpr (HAS_MASK) m = a.mask[idx];
-    if constexpr (kSepForm<L, R, C>) {
-        // nx a multiple of 32: every warp is 32 consecutive sites of one row
+    if constexpr (kPacked<R>) {
+        // nx a multiple of 32: every warp is 32 consecutive sites of one row,
+        // and a warp whose sites have no solid or outside neighbour takes the
+        // separable sums, or at least the code without bounce-back selections
         if ((a.nx & 31) == 0 && !(HAS_MASK && __any_sync(0xffffffffu, m != 0u))) {
-            moments_site_sep<L, C, MODE, IX>(a, idx);
+            if constexpr (kSepForm<L, R, C>) moments_site_sep<L, C, MODE, IX>(a, idx);
+            else moments_site_packed<L, C, false, MODE, IX>(a, idx, 0u);
             return;
         }
     }
@@ -446,12 +449,11 @@ __device__ __forceinline__ T ld_maybe_cg(const T *p)
 }
 
 // S0 + S2..S5 at site idx (0 <= idx < a.N).
-template <class L, class R, class C, bool HAS_MASK, int MODE, class IX, bool CG = false>
-__device__ __forceinline__ void collide_site(const SplitArgs<R, typename C::S> &a, const int idx)
+template <class L, class R, class C, bool HAS_MASK, int MODE, class IX, bool CG>
+__device__ __forceinline__ void collide_site_impl(const SplitArgs<R, typename C::S> &a, const int idx,
+                                                  const uint32_t m)
 {
     constexpr int D = L::D, Q = L::Q;
-    uint32_t m = 0;
-    if constexpr (HAS_MASK) m = a.mask[idx];
     if (m & kSolidBit) return;
     const IX N = (IX)a.N;
     const Nbr32 nb(idx, a.nx, a.ny, D == 3 ? a.nz : 1);
@@ -544,6 +546,28 @@ __device__ __forceinline__ void collide_site(const SplitArgs<R, typename C::S> &
     });
     if (!(isfinite(phi) && isfinite(P) && isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2])))
         atomicOr(a.err, 1);
+}
+
+// S0 + S2..S5 at site idx.  With FP32 arithmetic and nx a multiple of 32
+// (whole warps in one row), a warp whose sites have no solid or outside
+// neighbour runs the code without bounce-back selections (the same
+// arithmetic: with no mask bit set both give the same bits).  Not in the
+// even step of the in-place store: there the two copies of the code need
+// more registers than it has.
+template <class L, class R, class C, bool HAS_MASK, int MODE, class IX, bool CG = false>
+__device__ __forceinline__ void collide_site(const SplitArgs<R, typename C::S> &a, const int idx)
+{
+    uint32_t m = 0;
+    if constexpr (HAS_MASK) {
+        m = a.mask[idx];
+        if constexpr (kPacked<R> && MODE != kAAEven) {
+            if ((a.nx & 31) == 0 && !__any_sync(0xffffffffu, m != 0u)) {
+                collide_site_impl<L, R, C, false, MODE, IX, CG>(a, idx, 0u);
+                return;
+            }
+        }
+    }
+    collide_site_impl<L, R, C, HAS_MASK, MODE, IX, CG>(a, idx, m);
 }
 
 template <class L, class R, class C, bool HAS_MASK, int MODE, class IX>
