@@ -235,21 +235,30 @@ __device__ __forceinline__ void s1_pairs(const SiteConsts<R> &k, const R *hp, co
     phihat = k.clamp ? clamp01(phi) : phi;
     rho = k.rho_a + phihat * k.drho;
     const R kfac = R(3) / rho;                          // 1 / (T rho)
-    u[0] = R(0); u[1] = R(0); u[2] = R(0);
+    // u = sum_i (g_i + K_i) c_i, K_i = w_i/(T rho) {P(x-c_i) - P(x)}: the
+    // g differences and the weighted P differences are summed apart and
+    // 1/(T rho) applied once, as the split form's moments launch does
+    R ug[3] = {R(0), R(0), R(0)}, up[3] = {R(0), R(0), R(0)};
     sumg = gp[0];
     R swP = R(0);
     static_for<0, (L::Q - 1) / 2>([&](auto Pp) {
         constexpr int i = 2 * decltype(Pp)::value + 1;
         constexpr int io = i + 1;
         const R wi = R(L::w(i));
-        // (g_i + K_i) - (g_-i + K_-i), K_i = w_i/(T rho) {P(x-c_i) - P(x)}
-        const R t = (gp[i] - gp[io]) + wi * kfac * (Pn[i] - Pn[io]);
+        const R dg = gp[i] - gp[io], dp = wi * (Pn[i] - Pn[io]);
         static_for<0, 3>([&](auto A) {
             constexpr int a = decltype(A)::value;
-            if constexpr (L::c(i, a) != 0) acc_c<L::c(i, a)>(u[a], t);
+            if constexpr (L::c(i, a) != 0) {
+                acc_c<L::c(i, a)>(ug[a], dg);
+                acc_c<L::c(i, a)>(up[a], dp);
+            }
         });
         sumg = sumg + (gp[i] + gp[io]);
         swP = swP + wi * (Pn[i] + Pn[io]);
+    });
+    static_for<0, 3>([&](auto A) {
+        constexpr int a = decltype(A)::value;
+        u[a] = ug[a] + kfac * up[a];
     });
     sumK = kfac * (swP - R(1.0 - L::w(0)) * P0);
 }
@@ -418,18 +427,13 @@ __device__ __forceinline__ void collide_pairs(const SiteConsts<float> &k, float 
     const float Eg0 = bdiv - 1.5f * uu;
     const float p45 = 4.5f * phi;
 
-    // --- S4 and S5, rest direction
+    // --- S4 and S5, rest direction (h: after the pairs)
     const float w0 = float(L::w(0));
-    const float heq0 = w0 * Eh0;
     float geq0 = w0 * (-1.5f * uu) + (w0 - 1.f) * bdiv;
     if constexpr (!PDEV) geq0 = P * k.cP + geq0;
-    if constexpr (INIT) {
-        hs[0] = heq0;
-        gs[0] = geq0;
-    } else {
-        hs[0] = hp[0] - (hp[0] - heq0) * k.inv_tau_phi;
-    }
+    if constexpr (INIT) gs[0] = geq0;
     float eg[NP], og[NP], ne[NP];
+    float seh = 0.f;                                    // sum of the pairs' even h_eq parts
     static_for<0, NP>([&](auto Pp) {
         constexpr int p = decltype(Pp)::value;
         constexpr int i = 2 * p + 1;
@@ -438,6 +442,7 @@ __device__ __forceinline__ void collide_pairs(const SiteConsts<float> &k, float 
         const float cu2 = cu * cu;
         const float eh = wi * (Eh0 + p45 * cu2);
         const float oh = wi * dot_c<L, i>(Vh);
+        seh = __fadd_rn(seh, eh);                    // no contraction: every kernel rounds eh alike
         eg[p] = wi * (Eg0 + 4.5f * cu2);
         og[p] = wi * dot_c<L, i>(Vg);
         if constexpr (INIT) {
@@ -452,6 +457,14 @@ __device__ __forceinline__ void collide_pairs(const SiteConsts<float> &k, float 
             else ne[p] = (gp[i] + gp[i + 1]) - 2.f * eg[p];   // (g - g_eq) summed over the pair
         }
     });
+    // sum_i h_eq_i = phi (sum_i Gamma_i = 1, the odd parts cancel): the rest
+    // direction takes phi minus the moving directions, so the zeroth moment
+    // does not depend on the FP32 weights, whose sum exceeds 1 by 7e-9 (D2Q9,
+    // D3Q27) or 1.5e-8 (D3Q19) and would add that fraction of the phase mass
+    // every step.  In exact arithmetic this is w_0 phi (1 - u^2 / (2T)).
+    const float heq0 = phi - 2.f * seh;
+    if constexpr (INIT) hs[0] = heq0;
+    else hs[0] = hp[0] - (hp[0] - heq0) * k.inv_tau_phi;
     if constexpr (!INIT) {
         // Pi_ab = sum_k c_ka c_kb (g_k - g_eq_k), per pair (c_ka c_kb is even in c)
         float Pi[3][3];

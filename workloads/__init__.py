@@ -109,6 +109,37 @@ def droplet_2d(n: int = 64, R: float = 16.0, center=None, W: float = 4.0, ux: fl
 
 
 # ---------------------------------------------------------------------------
+# 2D rising bubble (Sec. III.D, Table tab_bubblerise)
+
+# (rho_1, mu_1, mu_2, sigma) of the two cases of the table; the bubble's
+# density rho_2 = 0.22, R = 50 at (100, 100) in a 200 x 400 domain, gravity
+# g = 1.36e-8 in -y (Sec. III.D).
+BUBBLE_CASES = {1: (2.2, 7.3e-3, 7.3e-4, 3.0e-5), 2: (220.0, 7.3e-1, 7.3e-3, 2.4e-4)}
+
+
+def rising_bubble_2d(case: int = 1, nx: int = 200, ny: int = 400, R: float = 50.0, center=(100.0, 100.0),
+                     g: float = 1.36e-8, W: float = 4.0, steps: int = 20000) -> Case:
+    """A light bubble (phi = 0, density 0.22) in a heavier liquid column
+    (phi = 1), gravity in -y.  The boundaries are not given in the paper:
+    periodic in x, solid rows at y = 0 and y = ny - 1 (halfway bounce-back).
+    Kinematic viscosities are the table's dynamic ones over the densities."""
+    rho1, mu1, mu2, sigma = BUBBLE_CASES[case]
+    rho2 = 0.22
+    x, y, _ = grid_coords(nx, ny, 1)
+    d = np.sqrt((x - center[0]) ** 2 + (y - center[1]) ** 2) - R   # positive in the liquid
+    phi = tanh_profile(d, W)
+    solid = np.zeros(phi.shape, np.uint8)
+    solid[:, 0, :] = 1
+    solid[:, -1, :] = 1
+    phi = np.where(solid.astype(bool), 0.0, phi)
+    params = base_params(rho_w=rho1, rho_a=rho2, nu_w=mu1 / rho1, nu_a=mu2 / rho2, sigma=sigma, W=W,
+                         g_ext=(0.0, -g, 0.0))
+    return Case(f"bubble2d_case{case}_{nx}x{ny}", "D2Q9", (nx, ny, 1), params, phi, np.zeros(phi.shape),
+                np.zeros((3,) + phi.shape), (1, 0, 1), solid, steps,
+                dict(R=R, center=center, rho1=rho1, rho2=rho2, g=g))
+
+
+# ---------------------------------------------------------------------------
 # 2D layered two-phase Poiseuille flow
 
 def two_layer_poiseuille_profile(y: np.ndarray, y_wall_lo: float, y_int: float, y_wall_hi: float,
