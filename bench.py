@@ -284,6 +284,7 @@ def run_ours(args):
     achieved = per_launch / t_launch / 1e9
     peak, peak_kind = measured_peaks()
     traffic = None
+    roofline_alu = None
     try:
         with open(TRAFFIC_FILE) as f:
             tr = json.load(f)
@@ -291,6 +292,17 @@ def run_ours(args):
         ent = tr.get(key, {})
         if ent.get("source_hash") == kernel_source_hash():
             traffic = ent["dram_bytes_per_step"]
+        if ent.get("flops_source_hash") == kernel_source_hash():
+            # FP32 operations per site update (fadd + fmul + 2 ffma, both launches, ncu);
+            # peak from the unit counts: SMs x 128 FP32 lanes x 2 flop x maximum SM clock
+            fps = ent["fp32_flops_per_site"]
+            sms = torch.cuda.get_device_properties(local).multi_processor_count
+            peak_alu = sms * 128 * 2 * 2.07e9 / 1e12
+            ach_alu = fps * N / t_launch / 1e12
+            roofline_alu = {"bound": "alu", "achieved": round(ach_alu, 2), "peak": round(peak_alu, 1),
+                            "unit": "TFLOP/s", "frac": round(ach_alu / peak_alu, 4),
+                            "flops_per_site": fps,
+                            "peak_kind": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
     except Exception:
         traffic = None
     e2e = None
@@ -357,6 +369,7 @@ def run_ours(args):
                                     if split else "step_kernel (fused S0..S5, one launch per step)"),
                          "store": "in-place AA" if args.inplace else "ping-pong",
                          "bytes_per_site": per_site},
+            "roofline_alu": roofline_alu,
             "e2e": e2e,
             "gpu_launches": args.steps * (2 if split else 1),
             "clocks": clk,
