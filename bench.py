@@ -292,6 +292,9 @@ def run_ours(args):
         ent = tr.get(key, {})
         if ent.get("source_hash") == kernel_source_hash():
             traffic = ent["dram_bytes_per_step"]
+    except Exception:
+        traffic, ent = None, {}
+    try:
         if ent.get("flops_source_hash") == kernel_source_hash():
             # FP32 operations per site update (fadd + fmul + 2 ffma, both launches, ncu);
             # peak from the unit counts: SMs x 128 FP32 lanes x 2 flop x maximum SM clock
@@ -304,7 +307,7 @@ def run_ours(args):
                             "flops_per_site": fps,
                             "peak_kind": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
     except Exception:
-        traffic = None
+        roofline_alu = None
     e2e = None
     if not args.no_e2e:
         # end to end through the C ABI: host fields (pinned) -> device -> K steps -> host fields
