@@ -463,8 +463,18 @@ __device__ __forceinline__ void collide_pairs(const SiteConsts<float> &k, float 
     // D3Q27) or 1.5e-8 (D3Q19) and would add that fraction of the phase mass
     // every step.  In exact arithmetic this is w_0 phi (1 - u^2 / (2T)).
     const float heq0 = phi - 2.f * seh;
-    if constexpr (INIT) hs[0] = heq0;
-    else hs[0] = hp[0] - (hp[0] - heq0) * k.inv_tau_phi;
+    if constexpr (INIT) {
+        hs[0] = heq0;
+    } else {
+        // The BGK step keeps sum_i h_i = phi (sum_i h_eq_i = phi), so the rest
+        // population is what the moving ones leave of phi, the sum of the
+        // pulled h: the rounding of the moving populations then does not
+        // accumulate in the phase mass.  In exact arithmetic this is
+        // h_0 - (h_0 - h_eq_0) / tau_phi.
+        float sm = 0.f;
+        static_for<1, L::Q>([&](auto I) { sm = __fadd_rn(sm, hs[decltype(I)::value]); });
+        hs[0] = __fsub_rn(phi, sm);
+    }
     if constexpr (!INIT) {
         // Pi_ab = sum_k c_ka c_kb (g_k - g_eq_k), per pair (c_ka c_kb is even in c)
         float Pi[3][3];
