@@ -484,3 +484,33 @@ def test_linear_stability_adopted_reading(phi_val):
 
 def test_printed_full_trace_filter_is_unstable():
     assert _spectral_radius(1.0, 0.0167, full_trace=True) > 1.01
+
+
+# ---------------------------------------------------------------------------
+# P16: the rising bubble's early rise against the added-mass closed form
+
+@pytest.mark.parametrize("case", [1, 2])
+def test_bubble_early_rise_added_mass(case):
+    """Sec. III.D, at half size (100 x 200, R = 25; the time scale
+    2R / sqrt(2Rg) is 60600 steps).  A 2D cylinder of density rho_2 in a
+    liquid of density rho_1 starts to accelerate at a = g (rho_1 - rho_2) /
+    (rho_2 + rho_1) (added mass of a circular cylinder, C_a = 1).  Drag, the
+    pressure waves that set up the hydrostatic state and the finite interface
+    only slow it, so after 10000 steps the rise lies below a t^2 / 2, and
+    this early not far below it.  A reversed gravity, a missing buoyancy
+    term or a doubled force falls outside [0.3, 1.02] of that value."""
+    c = W.rising_bubble_2d(case, nx=100, ny=200, R=25.0, center=(50.0, 50.0))
+    o = oracle.Oracle(c.lattice, c.shape, oracle.make_params(**c.params), periodic=c.periodic, solid=c.solid)
+    o.init(c.phi0, c.P0, c.u0)
+
+    def centroid_y(phi):
+        b = ((1.0 - phi) * (1 - c.solid))[0, 10:120, 10:90]
+        ys = np.arange(10, 120)[:, None]
+        return float((b * ys).sum() / b.sum())
+
+    t = 10000
+    o.step(t)
+    rise = centroid_y(o.fields()[0]) - centroid_y(c.phi0)
+    a = c.meta["g"] * (c.meta["rho1"] - c.meta["rho2"]) / (c.meta["rho2"] + c.meta["rho1"])
+    ideal = 0.5 * a * t * t
+    assert 0.3 * ideal <= rise <= 1.02 * ideal, f"rise {rise:.4f} vs inviscid {ideal:.4f}"
