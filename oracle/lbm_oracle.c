@@ -178,6 +178,35 @@ static void coords(const orc_state *s, long idx, int *x, int *y, int *z)
     *z = (int)(idx / ((long)s->nx * s->ny));
 }
 
+/* K_i = w_i / (T rho) { P(x - c_i) - P(x) }  (Eq. Kiterm) at site idx =
+ * (x, y, z) for the pressure field P (the previous step's P^n), with
+ * kfac = 1/(T rho); a solid or outside source x - c_i takes P(x).  The only
+ * evaluation of K_i: the S1 step (both its velocity and its pressure sums)
+ * and the pin entry point orc_k_terms call it. */
+static double k_term(const orc_state *s, const double *P, long idx, int x, int y, int z, int i, double kfac)
+{
+    const olat *L = &s->L;
+    long src = neighbour(s, x, y, z, -L->c[i][0], -L->c[i][1], -L->c[i][2]);
+    double Psrc = (src >= 0) ? P[src] : P[idx];
+    return L->w[i] * kfac * (Psrc - P[idx]);
+}
+
+/* w_i (c_i . u)|_{x - c_i}, the summand of the omega-term of P (Sec. II,
+ * pressure formula), for the velocity field u [3][N] (the previous step's
+ * u^n); a solid or outside source contributes u = 0.  Used by the S1 step
+ * and by orc_k_terms. */
+static double wcu_term(const orc_state *s, const double *u, long idx, int x, int y, int z, int i)
+{
+    const olat *L = &s->L;
+    const long N = s->N;
+    long src = neighbour(s, x, y, z, -L->c[i][0], -L->c[i][1], -L->c[i][2]);
+    double un[3];
+    int a;
+    (void)idx;
+    for (a = 0; a < 3; ++a) un[a] = (src >= 0) ? u[a * N + src] : 0.0;
+    return L->w[i] * (L->c[i][0] * un[0] + L->c[i][1] * un[1] + L->c[i][2] * un[2]);
+}
+
 /* Central-difference gradient and Laplacian of a scalar field f at site idx
  * (Sec. II, nearest-neighbour stencils):
  *   d_a f  = sum_i { f(x + c_i) - f(x - c_i) } c_ia w_i / (2T)
@@ -536,11 +565,7 @@ static void step_once(orc_state *s)
         rho = p->rho_a + phihat * (p->rho_w - p->rho_a);
         /* K_i = w_i / (T rho) { P(x - c_i) - P(x) }  (Eq. Kiterm), P = P^n */
         kfac = 3.0 / rho;                                    /* 1/(T rho) */
-        for (i = 0; i < Q; ++i) {
-            long src = neighbour(s, x, y, z, -L->c[i][0], -L->c[i][1], -L->c[i][2]);
-            double Psrc = (src >= 0) ? s->P[src] : s->P[idx];
-            K[i] = L->w[i] * kfac * (Psrc - s->P[idx]);
-        }
+        for (i = 0; i < Q; ++i) K[i] = k_term(s, s->P, idx, x, y, z, i, kfac);
         /* u = sum_i (g_i + K_i) c_i */
         for (a = 0; a < 3; ++a) {
             double acc = 0.0;
@@ -556,7 +581,7 @@ static void step_once(orc_state *s)
 #pragma omp parallel for schedule(static)
     for (idx = 0; idx < N; ++idx) {
         double rho, omega, sum_gK, sum_wcu, kfac;
-        int x, y, z, i, a;
+        int x, y, z, i;
         if (s->solid[idx]) continue;
         coords(s, idx, &x, &y, &z);
         rho = s->rho1[idx];
@@ -567,13 +592,9 @@ static void step_once(orc_state *s)
         sum_gK = 0.0;
         sum_wcu = 0.0;
         for (i = 0; i < Q; ++i) {
-            long src = neighbour(s, x, y, z, -L->c[i][0], -L->c[i][1], -L->c[i][2]);
-            double Psrc = (src >= 0) ? s->P[src] : s->P[idx];
-            double K = L->w[i] * kfac * (Psrc - s->P[idx]);
-            double un[3];
-            for (a = 0; a < 3; ++a) un[a] = (src >= 0) ? s->u[a * N + src] : 0.0;
+            double K = k_term(s, s->P, idx, x, y, z, i, kfac);
             sum_gK += s->gp[i * N + idx] + (1.0 + omega) * K;
-            sum_wcu += L->w[i] * (L->c[i][0] * un[0] + L->c[i][1] * un[1] + L->c[i][2] * un[2]);
+            sum_wcu += wcu_term(s, s->u, idx, x, y, z, i);
         }
         s->P1[idx] = rho_ref * T * sum_gK + omega * rho_ref * sum_wcu;
     }
@@ -675,27 +696,23 @@ int orc_grad_lap(void *vs, const double *f, int solid_mode, double *grad, double
 }
 
 /* K_i at every fluid site for a given P field and density field:
- * K [Q][N]; also sum_i w_i c_i . u(x - c_i) into wcu [N]. */
+ * K [Q][N]; also sum_i w_i c_i . u(x - c_i) into wcu [N].  Through the same
+ * k_term and wcu_term the S1 step evaluates (kfac = 3 / rho as there). */
 int orc_k_terms(void *vs, const double *P, const double *rho, const double *u, double *K, double *wcu)
 {
     orc_state *s = (orc_state *)vs;
-    const olat *L = &s->L;
     const long N = s->N;
     long idx;
     if (!s) return -1;
     for (idx = 0; idx < N; ++idx) {
         int x, y, z, i;
-        double acc = 0.0;
+        double acc = 0.0, kfac;
         if (s->solid[idx]) continue;
         coords(s, idx, &x, &y, &z);
-        for (i = 0; i < L->Q; ++i) {
-            long src = neighbour(s, x, y, z, -L->c[i][0], -L->c[i][1], -L->c[i][2]);
-            double Psrc = (src >= 0) ? P[src] : P[idx];
-            double un0 = (src >= 0) ? u[src] : 0.0;
-            double un1 = (src >= 0) ? u[N + src] : 0.0;
-            double un2 = (src >= 0) ? u[2 * N + src] : 0.0;
-            K[i * N + idx] = L->w[i] * (3.0 / rho[idx]) * (Psrc - P[idx]);
-            acc += L->w[i] * (L->c[i][0] * un0 + L->c[i][1] * un1 + L->c[i][2] * un2);
+        kfac = 3.0 / rho[idx];
+        for (i = 0; i < s->L.Q; ++i) {
+            K[i * N + idx] = k_term(s, P, idx, x, y, z, i, kfac);
+            acc += wcu_term(s, u, idx, x, y, z, i);
         }
         wcu[idx] = acc;
     }

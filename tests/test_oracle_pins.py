@@ -158,7 +158,11 @@ def test_filter_moments(lat, full):
 # ---------------------------------------------------------------------------
 # P4: nearest-neighbour stencils (Sec. II) are exact on quadratic fields, and
 # the K_i terms (Eq. Kiterm) satisfy sum K = lap(P)/(2 rho),
-# sum K c = -grad(P)/rho, sum w c.u(x-c) = -T div(u).
+# sum K c = -grad(P)/rho, sum w c.u(x-c) = -T div(u).  orc_k_terms evaluates
+# K_i and the omega-term summands through the same functions the S1 step
+# calls (k_term, wcu_term), so these identities pin the step's own code,
+# including its wall rule (a solid source contributes P(x) and u = 0, the
+# values the stencil takes for a solid neighbour).
 
 @pytest.mark.parametrize("lat,shape", [("D2Q9", (9, 8, 1)), ("D3Q19", (7, 6, 5)),
                                        ("D3Q27", (6, 7, 5))])
@@ -183,23 +187,31 @@ def test_stencil_exact_on_quadratics(lat, shape):
     assert np.abs(lap[inner] - want_l).max() < 1e-12 * scale
 
 
-@pytest.mark.parametrize("lat,shape", [("D2Q9", (12, 10, 1)), ("D3Q27", (6, 5, 7))])
-def test_k_term_identities(lat, shape):
+@pytest.mark.parametrize("lat,shape", [("D2Q9", (12, 10, 1)), ("D3Q19", (5, 6, 7)), ("D3Q27", (6, 5, 7))])
+@pytest.mark.parametrize("walls", [False, True])
+def test_k_term_identities(lat, shape, walls):
     r = rng(5)
-    o = oracle.Oracle(lat, shape)
+    periodic, solid = (1, 1, 1), None
+    if walls:
+        # closed in y, 10 % random solid sites
+        periodic = (1, 0, 1)
+        solid = (r.uniform(size=shape[::-1]) < 0.1).astype(np.uint8)
+    o = oracle.Oracle(lat, shape, periodic=periodic, solid=solid)
     N = o.N
+    fluid = np.ones(N, bool) if solid is None else solid.reshape(N) == 0
     P = r.normal(size=N) * 1e-3
     rho = r.uniform(1e-3, 1, N)
     u = np.zeros((3, N)); u[:o.d] = r.normal(size=(o.d, N)) * 1e-2
     K, wcu = o.k_terms(P, rho, u)
-    K = K.reshape(o.Q, N)
+    K = K.reshape(o.Q, N)[:, fluid]
     gP, lP = o.grad_lap(P)
-    gP = gP.reshape(3, N); lP = lP.reshape(N)
-    assert np.abs(K.sum(0) - lP / (2 * rho)).max() < 1e-12 * np.abs(lP / rho).max()
+    gP = gP.reshape(3, N)[:, fluid]; lP = lP.reshape(N)[fluid]
+    rf = rho[fluid]
+    assert np.abs(K.sum(0) - lP / (2 * rf)).max() < 1e-12 * np.abs(lP / rf).max()
     Kc = o.c.T.astype(float) @ K
-    assert np.abs(Kc - (-gP / rho)).max() < 1e-12 * np.abs(gP / rho).max()
-    div = sum(o.grad_lap(u[a])[0].reshape(3, N)[a] for a in range(o.d))
-    assert np.abs(wcu.reshape(N) - (-T * div)).max() < 1e-13
+    assert np.abs(Kc - (-gP / rf)).max() < 1e-12 * np.abs(gP / rf).max()
+    div = sum(o.grad_lap(u[a], solid_value_zero=True)[0].reshape(3, N)[a] for a in range(o.d))
+    assert np.abs(wcu.reshape(N)[fluid] - (-T * div[fluid])).max() < 1e-13
 
 
 # ---------------------------------------------------------------------------
@@ -489,6 +501,7 @@ def test_printed_full_trace_filter_is_unstable():
 # ---------------------------------------------------------------------------
 # P16: the rising bubble's early rise against the added-mass closed form
 
+@pytest.mark.slow
 @pytest.mark.parametrize("case", [1, 2])
 def test_bubble_early_rise_added_mass(case):
     """Sec. III.D, at half size (100 x 200, R = 25; the time scale
@@ -514,3 +527,174 @@ def test_bubble_early_rise_added_mass(case):
     a = c.meta["g"] * (c.meta["rho1"] - c.meta["rho2"]) / (c.meta["rho2"] + c.meta["rho1"])
     ideal = 0.5 * a * t * t
     assert 0.3 * ideal <= rise <= 1.02 * ideal, f"rise {rise:.4f} vs inviscid {ideal:.4f}"
+
+
+# ---------------------------------------------------------------------------
+# P17: shear-wave decay.  The target momentum equation (Sec. I, with the
+# stress tensor printed there) reduces for a small transverse wave
+# u_x = U sin(k y) in a single phase (grad rho = 0, div u = 0) to
+# du/dt = nu d2u/dy2, so the amplitude decays as exp(-nu k^2 t).  The
+# viscosity is the local one of Eq. tau_interpolate, nu = T (tau_mix - 1/2),
+# with tau_mix linear in phi: a slip in tau_k = nu_k / T + 1/2, in the mixing,
+# in nu, or in the filter's factor (1 - 1/tau) or w_i / (2 T^2) moves the rate
+# by far more than the 0.5 % allowed (the O(k^2) lattice correction at k =
+# 2 pi / 64 is below 0.1 %).
+
+def _mode_amplitude(f, mode):
+    return float((f * mode).sum() / (mode * mode).sum())
+
+
+@pytest.mark.parametrize("lat", LATTICES)
+@pytest.mark.parametrize("phi_val,nu_w,nu_a,nu_mix", [
+    (1.0, 0.0167, 0.167, 0.0167),
+    (0.0, 0.0167, 0.167, 0.167),
+    (0.3, 0.0167, 0.167, 0.167 + 0.3 * (0.0167 - 0.167)),
+    (1.0, 0.05, 0.05, 0.05),
+    (1.003, 0.0167, 0.167, 0.0167),
+    (-0.003, 0.0167, 0.167, 0.167),
+])
+def test_shear_wave_decay(lat, phi_val, nu_w, nu_a, nu_mix):
+    """A uniform mixture (phi = 0.3) checks the linear mixing of tau.  It is
+    not a steady state of the phase field with the paper's eps = 1e-10: the
+    normal n = grad phi / (|grad phi| + eps) turns rounding noise into unit
+    vectors and the theta n term of h_eq then separates the mixture (as the
+    conservative Allen-Cahn equation does).  With eps = 1 the theta n term is
+    a weak diffusion and the mixture stays uniform; the g step does not use
+    eps.  phi = 1.003 and -0.003 check the reading that clamps phi to [0, 1]
+    for the material properties: the bulk viscosities stay nu_w and nu_a
+    (unclamped, 1.003 would give 2.7 % less, and -0.003 a negative
+    density)."""
+    ny = 64
+    shape = (4, ny, 1) if lat == "D2Q9" else (4, ny, 2)
+    nx, _, nz = shape
+    extra = {"eps": 1.0} if phi_val not in (0.0, 1.0) else {}
+    o = oracle.Oracle(lat, shape, oracle.make_params(nu_w=nu_w, nu_a=nu_a, **extra))
+    k = 2 * np.pi / ny
+    y = np.broadcast_to(np.arange(ny, dtype=float)[None, :, None], (nz, ny, nx))
+    mode = np.sin(k * y)
+    u0 = np.zeros((3, nz, ny, nx))
+    u0[0] = 1e-4 * mode
+    o.init(np.full((nz, ny, nx), phi_val), np.zeros((nz, ny, nx)), u0)
+    t0, t1 = 200, 2000
+    o.step(t0)
+    a0 = _mode_amplitude(o.fields()[2][0], mode)
+    o.step(t1 - t0)
+    a1 = _mode_amplitude(o.fields()[2][0], mode)
+    rate = -np.log(a1 / a0) / (t1 - t0)
+    assert rate == pytest.approx(nu_mix * k * k, rel=5e-3)
+
+
+# ---------------------------------------------------------------------------
+# P18: plane acoustic wave.  Sec. I: the pressure equation and the momentum
+# equation combine into a sound wave of speed sqrt(T).  A standing wave
+# P = dP cos(k x), u = 0 in a single phase oscillates at omega = sqrt(T) k
+# and decays as exp(-Gamma k^2 t / 2), Gamma the longitudinal viscosity.
+# Gamma follows from the collision operator by a Chapman-Enskog expansion
+# (Sec. I, feq_expansion; the filter of Eq. LB_filter_col):
+#   - the filter relaxes the trace-free part of Pi with tau_mix, which gives
+#     the shear stress rho nu (grad u + grad u^T - (2/d) div u delta);
+#   - with the adopted reading the trace of Pi relaxes to equilibrium every
+#     step (a relaxation time of 1), which adds rho (T/2)(2/d) div u delta;
+#   - the B term of g_eq puts B div u delta into the equilibrium momentum
+#     flux, i.e. - rho B div u delta into the stress.
+# For a longitudinal wave that is
+#   Gamma = (4/3 - 2/d) nu + (2/3) lambda_b + T (1/d - 1/2).
+# With the printed filter (full Pi relaxed with tau_mix) the stress is
+# rho nu (grad u + grad u^T) - rho B div u delta, i.e.
+#   Gamma = (4/3) nu + (2/3) lambda_b - T/2,
+# which is negative at low nu (the printed form's instability).  The target
+# stress of Sec. I has Gamma = (4/3) nu + (2/3) lambda_b: the adopted reading
+# recovers its lambda_b term exactly and its nu term less (2/d) nu (d = 2) or
+# (2/3) nu + T/6 (d = 3).  A sign or coefficient slip in B (its nu, its
+# lambda_b, its T/2), in the trace handling or in K_i and the omega-term of P
+# (which set the sound speed) moves Gamma by 15 % or more; the lattice
+# correction at k = 2 pi / 64 is below 2 %.
+
+def _acoustic(lat, phi_val, nu, lam, full_trace, n=64, steps=3000, every=3):
+    from scipy.optimize import curve_fit
+
+    o = oracle.Oracle(lat, (n, 1, 1), oracle.make_params(nu_w=nu, nu_a=nu, lambda_b=lam,
+                                                         filter_full_trace=full_trace))
+    k = 2 * np.pi / n
+    mode = np.cos(k * np.arange(n, dtype=float))
+    dP = 1e-6
+    o.init(np.full((1, 1, n), phi_val), (dP * mode)[None, None, :], np.zeros((3, 1, 1, n)))
+    t, amp = [], []
+    for s in range(every, steps + 1, every):
+        o.step(every)
+        t.append(s)
+        amp.append(_mode_amplitude(o.fields()[1][0, 0], mode) / dP)
+    t, amp = np.array(t, float), np.array(amp)
+
+    def model(t, A, gam, om, ph):
+        return A * np.exp(-gam * t) * np.cos(om * t + ph)
+
+    (A, gam, om, ph), _ = curve_fit(model, t, amp, p0=[1.0, 1e-4, np.sqrt(T) * k, 0.0])
+    return 2 * gam / k ** 2, om / k
+
+
+@pytest.mark.parametrize("lat", ["D2Q9", "D3Q27"])
+@pytest.mark.parametrize("phi_val", [0.0, 1.0])
+@pytest.mark.parametrize("nu,lam", [(0.0167, 1.0 / 6.0), (0.167, 0.05), (0.05, 0.3)])
+def test_acoustic_wave_speed_and_damping(lat, phi_val, nu, lam):
+    d = 2 if lat == "D2Q9" else 3
+    gamma, c = _acoustic(lat, phi_val, nu, lam, full_trace=0)
+    assert c == pytest.approx(np.sqrt(T), rel=5e-3)
+    want = (4.0 / 3.0 - 2.0 / d) * nu + (2.0 / 3.0) * lam + T * (1.0 / d - 0.5)
+    assert gamma == pytest.approx(want, rel=3e-2)
+
+
+def test_acoustic_wave_printed_filter():
+    gamma, c = _acoustic("D2Q9", 1.0, 0.167, 1.0 / 6.0, full_trace=1)
+    assert c == pytest.approx(np.sqrt(T), rel=5e-3)
+    assert gamma == pytest.approx(4.0 / 3.0 * 0.167 + 2.0 / 9.0 * 0.5 - T / 2, rel=3e-2)
+
+
+# ---------------------------------------------------------------------------
+# P19: two-layer channel through the diffuse interface.  In steady layered
+# flow the momentum equation of Sec. I reduces to d/dy (rho nu du/dy) =
+# -rho g (div u = 0, so only the shear part of the stress acts).  The LB
+# carries nu d2u/dy2 through the filter and the rest, nu (du/dy)(drho/dy) /
+# rho, through the sigma . grad rho / rho^2 term of g_eq, so the steady
+# profile must solve that equation with the step's own phi(y), rho(phi) and
+# nu(phi) (halfway walls: u = 0 at y = 1/2 and ny - 3/2).  Across the
+# interface rho changes by 1000 times, so a wrong sign or factor in the stress
+# sigma_lm, in grad rho or in the rho^2 of that term leaves the light layer's
+# slope far from the solution; the lattice's own error is 1.5 %.
+
+def test_two_layer_channel_diffuse_interface_profile():
+    ny, g, nu_w, nu_a = 34, 5e-7, 0.011, 0.167
+    c = W.poiseuille_2d(nx=1, ny=ny, g=g, nu_w=nu_w, nu_a=nu_a, start_analytic=False)
+    o = oracle.Oracle("D2Q9", c.shape, oracle.make_params(**c.params), periodic=c.periodic, solid=c.solid)
+    o.init(c.phi0, c.P0, c.u0[:2])
+    o.step(150000)
+    phi, _, u = o.fields()
+    f = slice(1, ny - 1)
+    ux, ph = u[0, 0, f, 0], phi[0, f, 0]
+    p = c.params
+    phh = np.clip(ph, 0.0, 1.0)
+    rho = p["rho_a"] + phh * (p["rho_w"] - p["rho_a"])
+    tau = (3 * nu_a + 0.5) + phh * ((3 * nu_w + 0.5) - (3 * nu_a + 0.5))
+    mu = rho * (tau - 0.5) / 3
+    # conservative three-point form of d/dy (mu du/dy) = -rho g; a halfway
+    # wall is a ghost value -u one site out
+    n = ny - 2
+    A = np.zeros((n, n))
+    muh = 0.5 * (mu[1:] + mu[:-1])
+    for j in range(n):
+        if j > 0:
+            A[j, j - 1] += muh[j - 1]
+            A[j, j] -= muh[j - 1]
+        else:
+            A[j, j] -= 2 * mu[0]
+        if j < n - 1:
+            A[j, j + 1] += muh[j]
+            A[j, j] -= muh[j]
+        else:
+            A[j, j] -= 2 * mu[-1]
+    want = np.linalg.solve(A, -rho * g)
+    assert np.abs(ux - want).max() < 0.03 * want.max()
+    light = ph < 0.01
+    slope = np.polyfit(np.arange(light.sum()), ux[light], 1)[0]
+    slope_want = np.polyfit(np.arange(light.sum()), want[light], 1)[0]
+    assert slope == pytest.approx(slope_want, rel=0.03)
