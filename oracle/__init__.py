@@ -54,6 +54,7 @@ class Params(ctypes.Structure):
         ("g_ext", ctypes.c_double * 3),
         ("clamp_phi_props", ctypes.c_int32),
         ("filter_full_trace", ctypes.c_int32),
+        ("coupling_unew", ctypes.c_int32),
     ]
 
 

@@ -22,8 +22,9 @@
  * Readings where the paper is silent or ambiguous:
  *   - K_i uses P^n (previous step) at x and x - c_i; the omega-term of P uses
  *     u^n(x - c_i), the velocity of the previous step (one LKS pass started
- *     from the previous step).  Using u^{n+1} there instead makes the liquid
- *     unstable under shear next to walls and at nu < 5e-3.
+ *     from the previous step).  Using u^{n+1} there instead (coupling_unew =
+ *     1, the alternative reading) makes the liquid unstable under shear next
+ *     to walls and at nu < 5e-3.
  *   - The filter carries over only the trace-free part of Pi (the printed
  *     form, with the trace, is linearly unstable at the paper's viscosities);
  *     filter_full_trace = 1 restores the printed form.
@@ -67,6 +68,7 @@ typedef struct {
     double g_ext[3];
     int32_t clamp_phi_props;
     int32_t filter_full_trace; /* 0: trace-free Pi (default reading); 1: Pi as printed */
+    int32_t coupling_unew;     /* 0: the omega-term of P takes u^n (default reading); 1: u^{n+1} */
 } orc_params;
 
 typedef struct {
@@ -577,7 +579,8 @@ static void step_once(orc_state *s)
         s->rho1[idx] = rho;
     }
 
-    /* Second part of S1: the pressure; the omega-term takes u^n(x - c_i). */
+    /* Second part of S1: the pressure; the omega-term takes u^n(x - c_i)
+     * (u^{n+1}(x - c_i), from the first part, with coupling_unew). */
 #pragma omp parallel for schedule(static)
     for (idx = 0; idx < N; ++idx) {
         double rho, omega, sum_gK, sum_wcu, kfac;
@@ -594,7 +597,7 @@ static void step_once(orc_state *s)
         for (i = 0; i < Q; ++i) {
             double K = k_term(s, s->P, idx, x, y, z, i, kfac);
             sum_gK += s->gp[i * N + idx] + (1.0 + omega) * K;
-            sum_wcu += wcu_term(s, s->u, idx, x, y, z, i);
+            sum_wcu += wcu_term(s, p->coupling_unew ? s->u1 : s->u, idx, x, y, z, i);
         }
         s->P1[idx] = rho_ref * T * sum_gK + omega * rho_ref * sum_wcu;
     }

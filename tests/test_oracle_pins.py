@@ -466,8 +466,9 @@ def test_numpy_crosscheck():
 # Linear stability of the step (the reason for the trace-free reading of Pi):
 # Jacobian of one oracle step around a uniform state, spectral radius.
 
-def _spectral_radius(phi_val, nu, full_trace, n=8):
-    p = oracle.make_params(nu_w=nu, nu_a=nu, filter_full_trace=1 if full_trace else 0)
+def _spectral_radius(phi_val, nu, full_trace, n=8, coupling_unew=0):
+    p = oracle.make_params(nu_w=nu, nu_a=nu, filter_full_trace=1 if full_trace else 0,
+                           coupling_unew=coupling_unew)
     o = oracle.Oracle("D2Q9", (n, n, 1), p)
     o.init(np.full((1, n, n), phi_val), np.zeros((1, n, n)), np.zeros((2, 1, n, n)))
     h0, g0, P0, u0 = o.get_state()
@@ -496,6 +497,16 @@ def test_linear_stability_adopted_reading(phi_val):
 
 def test_printed_full_trace_filter_is_unstable():
     assert _spectral_radius(1.0, 0.0167, full_trace=True) > 1.01
+
+
+def test_unew_coupling_is_unstable_at_low_viscosity():
+    """The alternative reading of the pressure formula's omega-term (Sec. II),
+    u^{n+1}(x - c_i) in place of u^n(x - c_i): the liquid (phi = 1) grows at
+    the lowest viscosity the paper simulates, nu = 3.67e-4, where the adopted
+    reading is stable (test_linear_stability_adopted_reading); at nu =
+    0.0167 both are stable."""
+    assert _spectral_radius(1.0, 3.67e-4, full_trace=False, coupling_unew=1) > 1.003
+    assert _spectral_radius(1.0, 0.0167, full_trace=False, coupling_unew=1) < 1 + 1e-6
 
 
 # ---------------------------------------------------------------------------
@@ -610,11 +621,11 @@ def test_shear_wave_decay(lat, phi_val, nu_w, nu_a, nu_mix):
 # (which set the sound speed) moves Gamma by 15 % or more; the lattice
 # correction at k = 2 pi / 64 is below 2 %.
 
-def _acoustic(lat, phi_val, nu, lam, full_trace, n=64, steps=3000, every=3):
+def _acoustic(lat, phi_val, nu, lam, full_trace, n=64, steps=3000, every=3, **extra):
     from scipy.optimize import curve_fit
 
     o = oracle.Oracle(lat, (n, 1, 1), oracle.make_params(nu_w=nu, nu_a=nu, lambda_b=lam,
-                                                         filter_full_trace=full_trace))
+                                                         filter_full_trace=full_trace, **extra))
     k = 2 * np.pi / n
     mode = np.cos(k * np.arange(n, dtype=float))
     dP = 1e-6
@@ -642,6 +653,19 @@ def test_acoustic_wave_speed_and_damping(lat, phi_val, nu, lam):
     assert c == pytest.approx(np.sqrt(T), rel=5e-3)
     want = (4.0 / 3.0 - 2.0 / d) * nu + (2.0 / 3.0) * lam + T * (1.0 / d - 0.5)
     assert gamma == pytest.approx(want, rel=3e-2)
+
+
+@pytest.mark.parametrize("phi_val", [1.0, 0.5])
+def test_acoustic_wave_density_ratio_10(phi_val):
+    """At a density ratio of 10 the pressure formula's (1 + omega) rho_ref
+    must equal rho (omega of Sec. II with omega_max = rho_ratio and the
+    linear rho(phi) reading); a slip there (omega_max in place of
+    omega_max - 1, say) moves the sound speed by 5 %.  phi = 0.5 is a
+    uniform mixture, kept uniform with eps = 1 (see the shear-wave pin)."""
+    extra = {"rho_a": 0.1} if phi_val == 1.0 else {"rho_a": 0.1, "eps": 1.0}
+    gamma, c = _acoustic("D2Q9", phi_val, 0.0167, 1.0 / 6.0, full_trace=0, **extra)
+    assert c == pytest.approx(np.sqrt(T), rel=5e-3)
+    assert gamma == pytest.approx(0.0167 / 3 + 2.0 / 18.0, rel=3e-2)
 
 
 def test_acoustic_wave_printed_filter():
@@ -698,3 +722,33 @@ def test_two_layer_channel_diffuse_interface_profile():
     slope = np.polyfit(np.arange(light.sum()), ux[light], 1)[0]
     slope_want = np.polyfit(np.arange(light.sum()), want[light], 1)[0]
     assert slope == pytest.approx(slope_want, rel=0.03)
+
+
+# ---------------------------------------------------------------------------
+# P20: phase-field diffusion.  The phase-field LB recovers the conservative
+# Allen-Cahn equation of Sec. II, d phi/dt + div(phi u) = div[M (grad phi -
+# theta n)], with the mobility M = T (tau_phi - 1/2) of Eq.
+# LB_phi_filter_col.  A small wave phi = 1.001 + 5e-4 sin(k x) with
+# sigma = 0 (no capillary force, so u stays 0) and eps = 1 (so the theta n
+# term, quadratic in the perturbation, is negligible) decays at M k^2.  A
+# slip in tau_phi, in the BGK relaxation of h or in h_eq's first moment
+# (phi u + theta T n) moves the rate by more than the 0.3 % allowed; the
+# lattice and theta corrections are 0.1 - 0.17 % here.
+
+@pytest.mark.parametrize("lat", ["D2Q9", "D3Q27"])
+@pytest.mark.parametrize("M", [0.166, 0.05, 0.3])
+def test_phase_field_diffusion(lat, M):
+    n = 128
+    o = oracle.Oracle(lat, (n, 1, 1), oracle.make_params(sigma=0.0, eps=1.0, M=M))
+    k = 2 * np.pi / n
+    mode = np.sin(k * np.arange(n, dtype=float))
+    base = 1.001
+    o.init((base + 5e-4 * mode)[None, None, :], np.zeros((1, 1, n)), np.zeros((3, 1, 1, n)))
+    t0, t1 = 200, 8000
+    o.step(t0)
+    a0 = _mode_amplitude(o.fields()[0][0, 0] - base, mode)
+    o.step(t1 - t0)
+    phi, _, u = o.fields()
+    a1 = _mode_amplitude(phi[0, 0] - base, mode)
+    assert np.abs(u).max() == 0.0
+    assert -np.log(a1 / a0) / (t1 - t0) == pytest.approx(M * k * k, rel=3e-3)
