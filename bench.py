@@ -51,11 +51,19 @@ def parse():
     ap.add_argument("--storage", default="f32")
     ap.add_argument("--variant", type=int, default=0,
                     help="0 automatic (split form), 1 fused plane-synchronous, 2 fused pipelined, 3 split form, "
-                         "4 persistent split form")
+                         "4 persistent split form, 5 cluster step")
+    ap.add_argument("--cluster-rows", type=int, default=0, help="CTAs per cluster of the cluster step (0 auto)")
+    ap.add_argument("--staged", type=int, default=-1,
+                    help="cluster step: stage the pulled rows by bulk copies (-1 auto, 0 no, 1 yes)")
+    ap.add_argument("--zchunk", type=int, default=0, help="planes per CTA of the fused / cluster kernels (0 auto)")
     ap.add_argument("--inplace", action="store_true", help="one population store, AA streaming")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
-    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-requests", type=int, default=100,
+                    help="requests of the serving sample: the first ones of the seeded 2000-request trace, "
+                         "with its full 500..5000-step range")
+    ap.add_argument("--no-storage-forms", action="store_true",
+                    help="skip the FP16 / BF16 storage lines of the same workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="impact", choices=["impact", "bubble1", "bubble2"],
                     help="impact: the 3D droplet impact (default); bubble1/2: the 2D rising bubble of "
@@ -176,27 +184,78 @@ def cpu_baseline(reps_target_s: float = 10.0):
 
 
 def serving(n_requests: int):
-    """Served solves/s and p50/p99 latency on a bounded sample of the serving
-    workload: oscillating ellipsoidal droplets in periodic boxes of edge
-    {32, 48, 64, 96, 128}, density ratio 10..1000, sigma 5e-4..2e-3, FP32
-    arithmetic with FP16 storage, in-place stores; steps drawn from 50..500
-    (the full workload's 500..5000, scaled by 1/10 to bound the run).
+    """Served solves/s and p50/p99 latency on the serving workload: the first
+    n_requests of the seeded 2000-request trace (oscillating ellipsoidal
+    droplets in periodic boxes of edge {32, 48, 64, 96, 128}, density ratio
+    10..1000, sigma 5e-4..2e-3, 500..5000 steps each), FP32 arithmetic with
+    FP16 storage, in-place stores.
     1) closed loop: all requests at t = 0 -> capacity (solves/s);
     2) open loop: Poisson arrivals at 0.8 x capacity -> p50/p99 latency;
     3) the same open-loop trace one request at a time (FP32, split form)."""
     from paper_2512_01027_gb300.serving import Server, run_one_at_a_time
 
-    closed = W.request_trace(n=n_requests, rate=1e9, steps_range=(50, 500))
+    full = 2000
+    closed = W.request_trace(n=full, rate=1e9)[:n_requests]
     srv = Server("D3Q27", "f16", inplace=True, chunk=16)
     cl = srv.run(closed).summary()
     cap = cl["solves_per_s"]
     rate = 0.8 * cap
-    opened = W.request_trace(n=n_requests, rate=rate, steps_range=(50, 500))
+    opened = W.request_trace(n=full, rate=rate)[:n_requests]
     op = srv.run(opened).summary()
     srv.close()
     seq = run_one_at_a_time(opened, storage="f32").summary()
-    return {"workload": f"{n_requests} requests, D3Q27 droplets, edges 32..128, 50..500 steps, f16 storage",
+    work = sum(r.edge ** 3 * r.steps for r in closed)
+    return {"workload": f"first {n_requests} of the 2000-request trace ({100.0 * n_requests / full:.0f} %), "
+                        f"D3Q27 droplets, edges 32..128, 500..5000 steps, f16 storage, "
+                        f"{work / 1e9:.0f} G site updates",
+            "fraction_of_trace": n_requests / full,
             "closed_loop": cl, "open_loop": dict(op, arrival_rate_per_s=rate), "one_at_a_time_f32": seq}
+
+
+def storage_form(args, c, storage: str, f32_ms: float):
+    """The same workload with populations stored in 16 bits (FP32 arithmetic),
+    timed like the main line: MLUPS and the HBM roofline at its own
+    algorithmic bytes per site."""
+    import torch
+
+    import paper_2512_01027_gb300 as lbm
+
+    prm = {k: v for k, v in c.params.items() if k != "g_ext"}
+    L = lbm.Lattice(c.lattice, c.shape, periodic=c.periodic, solid=c.solid, storage=storage,
+                    g_ext=c.params["g_ext"], inplace=int(args.inplace), **prm)
+    form = "split form"
+    if args.variant:
+        try:
+            if args.cluster_rows or args.staged != -1:
+                L.set_cluster(args.cluster_rows, args.staged)
+            L.set_tuning(args.variant, args.zchunk)
+            form = f"variant {args.variant}"
+        except lbm.LbmError:
+            pass                      # this storage has no such launch form: the split form
+    stream = torch.cuda.current_stream()
+    L.set_stream(stream)
+    L.init_fields(c.phi0, c.P0, c.u0)
+    L.step(args.warmup)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    L.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    L.check()
+    L.close()
+    per_site = alg_bytes_per_site(27, 3, 2, 4)
+    t_step = ms / args.steps / 1e3
+    achieved = per_site * c.N / t_step / 1e9
+    peak, peak_kind = measured_peaks()
+    return {"value": round(c.N / t_step / 1e6, 2), "unit": UNIT, "ms_per_step": ms / args.steps,
+            "speedup_vs_f32": round(f32_ms / (ms / args.steps), 4),
+            "dtype": f"{storage}-storage/f32", "form": form,
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "bytes_per_site": per_site, "peak_kind": peak_kind},
+            "gpu_launches": (2 if form == "split form" else 1) * args.steps}
 
 
 def dist_init():
@@ -248,9 +307,21 @@ def run_ours(args):
     prm = {k: v for k, v in c.params.items() if k != "g_ext"}
     L = lbm.Lattice(c.lattice, c.shape, periodic=c.periodic, solid=c.solid, storage=args.storage,
                     g_ext=c.params["g_ext"], inplace=int(args.inplace), **prm)
+    if args.cluster_rows or args.staged != -1:
+        L.set_cluster(args.cluster_rows, args.staged)
     if args.variant:
-        L.set_tuning(args.variant, 0)
+        L.set_tuning(args.variant, args.zchunk)
     split = args.inplace or args.variant in (0, 3)
+    form = "split" if split else f"v{args.variant}"
+    kernel_name = {
+        "split": "moments_kernel + collide_kernel (split form, one step = both launches)",
+        "v1": "step_kernel (fused S0..S5, one launch per step)",
+        "v2": "step_kernel_v2 (fused S0..S5, pipelined, one launch per step)",
+        "v4": "split_persistent_kernel (both split phases in one launch per step)",
+        "v5": "cluster_step_kernel (one launch per step; clusters share each plane's moments in "
+              "distributed shared memory)",
+    }[form]
+    launches_per_step = 2 if split else 1
     stream = torch.cuda.current_stream()
     L.set_stream(stream)
     L.init_fields(c.phi0, c.P0, c.u0)
@@ -288,7 +359,7 @@ def run_ours(args):
     try:
         with open(TRAFFIC_FILE) as f:
             tr = json.load(f)
-        key = f"n{args.n}-{args.storage}-{'split' if split else 'v%d' % args.variant}{'-inplace' if args.inplace else ''}"
+        key = f"n{args.n}-{args.storage}-{form}{'-inplace' if args.inplace else ''}"
         ent = tr.get(key, {})
         if ent.get("source_hash") == kernel_source_hash():
             traffic = ent["dram_bytes_per_step"]
@@ -343,6 +414,10 @@ def run_ours(args):
                         f"{ke} steps, read_fields to pinned host"}
 
     state_gb = L.footprint()[0] / 1e9
+    forms = None
+    if not args.no_storage_forms and args.storage == "f32" and world == 1:
+        L.close()
+        forms = {st: storage_form(args, c, st, ms / args.steps) for st in ("f16", "bf16")}
     serve = None
     if not args.no_serve:
         L.close()
@@ -368,15 +443,15 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "peak_kind": peak_kind,
-                         "kernel": ("moments_kernel + collide_kernel (split form, one step = both launches)"
-                                    if split else "step_kernel (fused S0..S5, one launch per step)"),
+                         "kernel": kernel_name,
                          "store": "in-place AA" if args.inplace else "ping-pong",
                          "bytes_per_site": per_site},
             "roofline_alu": roofline_alu,
             "e2e": e2e,
-            "gpu_launches": args.steps * (2 if split else 1),
+            "gpu_launches": args.steps * launches_per_step,
             "clocks": clk,
             "cpu_baseline": cpu,
+            "storage_forms": forms,
             "serving": serve,
         }
         print(json.dumps(line), flush=True)

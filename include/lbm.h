@@ -97,6 +97,12 @@ typedef struct {
     int32_t inplace;           /* 0: two population stores (ping-pong, default); 1: one store
                                   updated in place with the AA streaming pattern (half the
                                   population memory; steps run in the two-launch split form) */
+    int32_t coupling_unew;     /* 0: the omega-term of the pressure formula (Sec. II) takes
+                                  u^n(x - c_i), the previous step's velocity (default);
+                                  1: u^{n+1}(x - c_i) of the same step, the alternative
+                                  reading, linearly unstable at nu < 5e-3 (split form and
+                                  batches only: the fused, persistent and cluster forms
+                                  return LBM_ERR_UNSUPPORTED) */
 } lbm_params;
 
 /* Fill *p with the paper's defaults: rho_w = 1, rho_a = 1e-3, nu_w = 0.0167,
@@ -209,15 +215,34 @@ int lbm_load_state(lbm_handle h, const void *host_buf, size_t bytes);
  * stencils + collisions), 4 = persistent split form (both phases in one
  * launch per step: blocks take plane-ordered work items so that the
  * collision of a plane follows the moments of the next one while their data
- * is in L2; FP32 arithmetic and Q x sites < 2^32, else LBM_ERR_UNSUPPORTED).
+ * is in L2; FP32 arithmetic and Q x sites < 2^32, else LBM_ERR_UNSUPPORTED),
+ * 5 = cluster step (one launch per step: a CTA owns one row of sites and
+ * marches in z, a thread-block cluster of CTAs on consecutive rows shares
+ * the moments of each plane through distributed shared memory, so the
+ * moments reach the stencils without passing through HBM; 3D lattices,
+ * ping-pong store, nx a multiple of 32 and at most 256, ny a multiple of
+ * the cluster rows (lbm_set_cluster), 2 nx a multiple of 32 x rows,
+ * Q x sites < 2^32, FP64, FP32 or FP16 storage; else LBM_ERR_UNSUPPORTED).
  * An in-place handle always uses a split form (variants 1 and 2 are
  * LBM_ERR_UNSUPPORTED there).  zchunk: z planes per
- * block of the fused kernels (0 = automatic); it never changes results.
+ * block of the fused kernels and per CTA of the cluster step (0 =
+ * automatic); it never changes results.
  * Every variant evaluates the same formulas in the same order: with FP64
  * storage (built without FMA contraction) all variants agree bit for bit;
  * with FP32 arithmetic the compiler may contract a product and a sum into
  * one FMA differently in different kernels, so variants agree to rounding. */
 int lbm_set_tuning(lbm_handle h, int variant, int zchunk);
+
+/* Shape of the cluster step (variant 5).  rows: CTAs per thread-block
+ * cluster, one of 2, 4, 8, 16, or 0 for automatic (the largest the lattice
+ * fits, 16 only where the device allows clusters of that non-portable
+ * size).  staged: with FP32 arithmetic (FP32 or FP16 storage), 1 or -1
+ * (default) stages the population rows each plane pulls in shared memory by
+ * bulk asynchronous copies two planes ahead; 0 reads them from the store.
+ * Neither changes results.  LBM_ERR_INVALID_ARG for other values,
+ * LBM_ERR_UNSUPPORTED when the lattice does not meet the cluster step's
+ * requirements with that many rows. */
+int lbm_set_cluster(lbm_handle h, int rows, int staged);
 
 /* Testing aid for the failure path of the persistent split step (variant
  * 4): while set, its moments launch leaves the z-plane `plane` uncounted, so
@@ -241,9 +266,10 @@ int lbm_estimate_footprint(const lbm_grid *grid, int lattice, const lbm_params *
 /* Allocation-free FP64 sums of caller-owned device fields; the paper has no
  * counterpart (it is a service for callers, not a step of the method).
  * For callers that cannot allocate device memory where they need the sums:
- * work being recorded into a CUDA graph by stream capture (cudaMalloc cannot
- * be captured), real-time loops that must not block in an allocator, and
- * hosts whose device memory belongs to a pool they do not own.
+ * real-time loops that must not block in an allocator (cudaMalloc and
+ * cudaFree can synchronise the device), and hosts whose device memory
+ * belongs to a pool they do not own, where an allocation of the library's
+ * own would escape the pool's accounting.
  * Inputs: d_phi[n], d_u[3][n] (device doubles, e.g. from
  * lbm_read_fields_device), d_solid[n] (device bytes, 1 = solid, or NULL),
  * rho_w > rho_a > 0 and clamp_phi_props as in lbm_params.  Output: d_out[5]
@@ -255,12 +281,17 @@ int lbm_estimate_footprint(const lbm_grid *grid, int lattice, const lbm_params *
  * partial sums live in one fixed 40 KB array (1024 blocks x 5 doubles) in
  * device global memory that every GPU loading this library holds until the
  * process exits.  Limit: 1 <= n <= 2^31 - 1 sites; larger n (or n <= 0)
- * returns LBM_ERR_INVALID_ARG.  The first call with a given device current
- * looks up the array's device address (cudaGetSymbolAddress) and caches it;
- * make that first call before any stream capture.  All calls share the
- * array and it keeps the last call's contents (each call overwrites every
- * partial it reads, so nothing needs clearing); calls that overlap on the
- * GPU (different streams, or different host threads) race on it. */
+ * returns LBM_ERR_INVALID_ARG, as do NULL d_phi, d_u or d_out and densities
+ * other than rho_w > rho_a > 0.  The first call with a given device current
+ * looks up the array's device address (cudaGetSymbolAddress) and caches it
+ * for as long as that device's context lives (after cudaDeviceReset the
+ * library must be loaded again); make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents
+ * (each call overwrites every partial it reads, so nothing needs clearing);
+ * calls that overlap on the GPU (different streams, or different host
+ * threads) race on it.  LBM_ERR_CUDA when a launch fails; the error state
+ * of the calling thread is read without clearing it, so an error pending
+ * from earlier work is reported too and stays pending for the caller. */
 int lbm_reduce_fields_noalloc(const double *d_phi, const double *d_u, const uint8_t *d_solid, int64_t n,
                               double rho_w, double rho_a, int32_t clamp_phi_props, double *d_out, void *stream);
 
@@ -271,8 +302,9 @@ const char *lbm_last_error(lbm_handle h);
 /* ------------------------------------------------------------------------
  * Autotuner.  Times `trial_steps` steps of every launch form the handle
  * supports (split form; persistent split form; fused plane-synchronous
- * kernel; fused pipelined kernel at several z-chunks, where available) on
- * the handle's own state,
+ * kernel; fused pipelined kernel at several z-chunks; cluster step with
+ * clusters of 4, 8 and 16 rows, staged or not, where available) on the
+ * handle's own state,
  * keeps the fastest with lbm_set_tuning and restores the state it started
  * from (through a host copy of lbm_state_bytes bytes), so the results of the
  * following steps are those of the chosen variant from the same state.
@@ -313,6 +345,27 @@ int lbm_batch_set_stream(lbm_batch b, void *stream);
 /* chunk: steps per graph launch, 1..64 (default 16); use_graph: 0 launches
  * the kernels one by one (same results). */
 int lbm_batch_set_tuning(lbm_batch b, int chunk, int use_graph);
+
+/* Launch shape of the batch kernels: span = consecutive blocks of 128 sites
+ * (one thread a site) that one work item covers, 1..16 (default 1; a longer
+ * item pays the member lookup and the load of the member's arguments once
+ * for more sites, a shorter one spreads small members over more blocks);
+ * blocks_per_sm = persistent blocks per SM, 0 (default: as many as fit) to
+ * 32 (capped at what fits).  Neither changes results. */
+int lbm_batch_set_shape(lbm_batch b, int span, int blocks_per_sm);
+
+/* Autotuner of the batch: times `trial_steps` steps (rounded up to whole
+ * chunks) of the current members for each launch shape it tries (chunk 8,
+ * 16, 32; span 1, 2, 4, 8; all resident blocks or one block per SM fewer),
+ * keeps the fastest (lbm_batch_set_tuning / lbm_batch_set_shape), then
+ * restores every member's state (through host copies of lbm_state_bytes
+ * bytes, as lbm_autotune does) and its step budget, so the following steps
+ * give the results they would have given without the trials.  Outputs (any
+ * may be NULL): the chosen chunk, span, blocks per SM and the measured
+ * milliseconds per step.  LBM_ERR_INVALID_ARG for an empty batch or
+ * trial_steps outside 1..1000.  Synchronises. */
+int lbm_batch_autotune(lbm_batch b, int trial_steps, int *chunk, int *span, int *blocks_per_sm,
+                       double *ms_per_step);
 
 /* Adds h with a budget of `steps` steps (>= 0).  h must match the batch's
  * lattice and storage and belong to no other batch (else

@@ -44,6 +44,13 @@
  *   - The 2/3 factors of B and of the bulk stress term are used as printed,
  *     also for the 2D lattice.
  *
+ * Pins (tests/test_oracle_pins.py) check every function here against
+ * closed forms, invariants and special cases, except one term: the bulk part
+ * of the stress, rho (2/3)(lambda_b - nu) div(u) delta, which enters only
+ * through sigma . grad(rho) / rho^2 in g_eq.  No closed form isolates it, so
+ * its parity is unpinned: only the independent NumPy transcription
+ * (crosscheck_np.py) checks it.
+ *
  * Layout: populations are [Q][N], N = nx*ny*nz, x fastest.  Vector fields
  * are [3][N] (z component zero in 2D).
  */

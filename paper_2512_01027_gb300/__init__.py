@@ -50,7 +50,8 @@ class Params(ctypes.Structure):
         "phi_m", "D", "eps")] + [("g_ext", ctypes.c_double * 3),
                                 ("clamp_phi_props", ctypes.c_int32),
                                 ("filter_full_trace", ctypes.c_int32),
-                                ("storage", ctypes.c_int32), ("inplace", ctypes.c_int32)]
+                                ("storage", ctypes.c_int32), ("inplace", ctypes.c_int32),
+                                ("coupling_unew", ctypes.c_int32)]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -85,6 +86,7 @@ SIGNATURES = {
     "lbm_save_state": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     "lbm_load_state": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     "lbm_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "lbm_set_cluster": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "lbm_footprint": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t)]),
     "lbm_reduce_fields_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _i64, ctypes.c_double, ctypes.c_double,
                                                   ctypes.c_int32, _vp, _vp]),
@@ -98,6 +100,9 @@ SIGNATURES = {
     "lbm_batch_destroy": (ctypes.c_int, [_vp]),
     "lbm_batch_set_stream": (ctypes.c_int, [_vp, _vp]),
     "lbm_batch_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "lbm_batch_set_shape": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "lbm_batch_autotune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _dp]),
     "lbm_batch_add": (ctypes.c_int, [_vp, _vp, _i64]),
     "lbm_batch_remove": (ctypes.c_int, [_vp, _vp]),
     "lbm_batch_step": (ctypes.c_int, [_vp, _i64, ctypes.POINTER(ctypes.c_int)]),
@@ -359,8 +364,13 @@ class Lattice:
 
     def set_tuning(self, variant: int = 0, zchunk: int = 0):
         """variant 0 auto, 1 fused plane-synchronous, 2 fused pipelined, 3 split form,
-        4 persistent split form; zchunk 0 = auto."""
+        4 persistent split form, 5 cluster step; zchunk 0 = auto."""
         _check(lib().lbm_set_tuning(self._h, int(variant), int(zchunk)), self._h)
+
+    def set_cluster(self, rows: int = 0, staged: int = -1):
+        """Cluster step shape: CTAs (rows) per cluster (0 = auto) and whether the
+        pulled rows are staged by bulk copies (-1 = auto, 0 = no, 1 = yes)."""
+        _check(lib().lbm_set_cluster(self._h, int(rows), int(staged)), self._h)
 
     def debug_stall(self, plane: int):
         """Testing aid of the persistent step's failure path (see lbm.h)."""
@@ -418,6 +428,19 @@ class Batch:
 
     def set_tuning(self, chunk: int = 16, use_graph: bool = True):
         _bcheck(lib().lbm_batch_set_tuning(self._b, int(chunk), int(bool(use_graph))), self._b)
+
+    def set_shape(self, span: int = 1, blocks_per_sm: int = 0):
+        """Work item span (blocks of 128 sites) and persistent blocks per SM (0 = all that fit)."""
+        _bcheck(lib().lbm_batch_set_shape(self._b, int(span), int(blocks_per_sm)), self._b)
+
+    def autotune(self, trial_steps: int = 32):
+        """Time the launch shapes on the current members, keep the fastest,
+        restore every member's state and budget.  Returns (chunk, span,
+        blocks_per_sm, ms_per_step)."""
+        K, sp, bps, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _bcheck(lib().lbm_batch_autotune(self._b, int(trial_steps), ctypes.byref(K), ctypes.byref(sp),
+                                         ctypes.byref(bps), ctypes.byref(ms)), self._b)
+        return K.value, sp.value, bps.value, ms.value
 
     def add(self, lat: "Lattice", steps: int):
         _bcheck(lib().lbm_batch_add(self._b, lat.handle, int(steps)), self._b)

@@ -45,6 +45,7 @@ HostConsts make_consts(const lbm_params &p)
     h.g[2] = p.g_ext[2];
     h.clamp = p.clamp_phi_props ? 1 : 0;
     h.full_trace = p.filter_full_trace ? 1 : 0;
+    h.coupling = p.coupling_unew ? 1 : 0;
     return h;
 }
 
@@ -164,7 +165,8 @@ int sync_and_check(lbm_ctx *c)
     int flag = 0;
     e = cudaMemcpy(&flag, c->d_err, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy(err flag)");
-    if (flag & 2) return fail(c, LBM_ERR_TIMEOUT, "a wait of the persistent step ran out (results invalid)");
+    if (flag & 2)
+        return fail(c, LBM_ERR_TIMEOUT, "a bounded wait of the persistent or cluster step ran out (results invalid)");
     if (flag) return fail(c, LBM_ERR_NONFINITE, "a step produced a non-finite phi, P or u");
     return LBM_OK;
 }
@@ -304,8 +306,9 @@ int lbm_create(const lbm_grid *grid, int lattice, const lbm_params *params, lbm_
         return fail(nullptr, LBM_ERR_INVALID_ARG,
                     "invalid parameters (need rho_w > rho_a > 0, nu > 0, M > 0, W > 0, D > 0)");
     const int storage = p.storage;
-    if (storage_bytes(storage) == 0 || (p.inplace != 0 && p.inplace != 1))
-        return fail(nullptr, LBM_ERR_INVALID_ARG, "unknown storage, or inplace not 0/1");
+    if (storage_bytes(storage) == 0 || (p.inplace != 0 && p.inplace != 1) ||
+        (p.coupling_unew != 0 && p.coupling_unew != 1))
+        return fail(nullptr, LBM_ERR_INVALID_ARG, "unknown storage, or inplace / coupling_unew not 0/1");
     const Ops *ops = ops_for(lattice, storage);
     if (!ops) return fail(nullptr, LBM_ERR_UNSUPPORTED, "lattice/storage combination not built");
 
@@ -678,15 +681,46 @@ int lbm_load_state(lbm_handle h, const void *host_buf, size_t bytes)
 int lbm_set_tuning(lbm_handle h, int variant, int zchunk)
 {
     if (!h) return LBM_ERR_INVALID_ARG;
-    if (variant < 0 || variant > 4 || zchunk < 0) return fail(h, LBM_ERR_INVALID_ARG, "variant in 0..4, zchunk >= 0");
+    if (variant < 0 || variant > 5 || zchunk < 0) return fail(h, LBM_ERR_INVALID_ARG, "variant in 0..5, zchunk >= 0");
+    if (variant == 5) {
+        if (h->consts.coupling)
+            return fail(h, LBM_ERR_UNSUPPORTED, "coupling_unew = 1 steps in the split form only");
+        bool ok = false;
+        if (h->cluster_rows > 0) ok = h->ops->cluster_ok(h, h->cluster_rows);
+        else
+            for (int r : {8, 4, 2}) ok = ok || h->ops->cluster_ok(h, r);
+        if (!ok)
+            return fail(h, LBM_ERR_UNSUPPORTED,
+                        "the cluster step needs a 3D lattice, a ping-pong store, nx a multiple of 32 and at most "
+                        "256, ny a multiple of the cluster rows, 2 nx a multiple of 32 x rows, Q * sites < 2^32 "
+                        "and no BF16 storage");
+        h->variant = 5;
+        h->cluster_zchunk = zchunk;
+        return LBM_OK;
+    }
     if (variant == 4 && !h->ops->persist_ok(h))
         return fail(h, LBM_ERR_UNSUPPORTED, "the persistent step needs FP32 arithmetic and Q * sites < 2^32");
     if (variant == 2 && !h->ops->has_v2())
         return fail(h, LBM_ERR_UNSUPPORTED, "pipelined kernel needs a 3D lattice with FP32 populations");
     if (h->inplace && (variant == 1 || variant == 2))
         return fail(h, LBM_ERR_UNSUPPORTED, "an in-place store streams with the split form only");
+    if (h->consts.coupling && variant != 0 && variant != 3)
+        return fail(h, LBM_ERR_UNSUPPORTED, "coupling_unew = 1 steps in the split form only");
     h->variant = variant;
     if (h->D == 3) h->zchunk = zchunk > 0 ? (zchunk < h->nz ? zchunk : h->nz) : h->zchunk_auto;
+    return LBM_OK;
+}
+
+int lbm_set_cluster(lbm_handle h, int rows, int staged)
+{
+    if (!h) return LBM_ERR_INVALID_ARG;
+    if (rows != 0 && rows != 2 && rows != 4 && rows != 8 && rows != 16)
+        return fail(h, LBM_ERR_INVALID_ARG, "rows in {0, 2, 4, 8, 16}");
+    if (staged < -1 || staged > 1) return fail(h, LBM_ERR_INVALID_ARG, "staged in {-1, 0, 1}");
+    if (rows != 0 && !h->ops->cluster_ok(h, rows))
+        return fail(h, LBM_ERR_UNSUPPORTED, "the cluster step cannot use clusters of that many rows here");
+    h->cluster_rows = rows;
+    h->cluster_stage = staged == 0 ? 0 : 1;
     return LBM_OK;
 }
 

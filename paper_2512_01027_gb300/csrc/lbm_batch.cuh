@@ -10,7 +10,11 @@
 //
 // Table: BatchHeader, then members sorted by the number of steps they take
 // in the chunk (descending).  Launch k of the chunk (0 <= k < K) covers the
-// first active[k] items: exactly the members with take > k.
+// first active[k] items: exactly the members with take > k.  An item is
+// `span` consecutive blocks of kSplitThreads sites of one member (span is in
+// the header: a longer item pays the member lookup and the argument loads
+// once for more sites, a shorter one balances small members better; the
+// batch autotuner picks it).
 #pragma once
 
 #include "lbm_split.cuh"
@@ -56,23 +60,28 @@ __global__ void __launch_bounds__(kSplitThreads, 3)
     using S = typename C::S;
     const int nmem = (int)hdr->nmem;
     const long long total = hdr->active[k];
+    const int span = (int)hdr->span;
     for (long long t = blockIdx.x; t < total; t += gridDim.x) {
         const int j = batch_find(mem, nmem, t);
         const int q = k & 1;
         SplitArgs<R, S> a = mem[j].a[q];
         a.seed += (unsigned)(k - q);   // a[q] holds the chunk's first steps; step k of the chunk
         const int mode = mem[j].mode[q];
-        const long long lidx = (t - mem[j].first_item) * kSplitThreads + threadIdx.x;
-        if (lidx >= a.N) continue;
-        const int idx = (int)lidx;
-        if (mem[j].has_mask) {
-            if (mode == kPingPong) batch_site<L, R, C, PHASE, true, kPingPong>(a, idx);
-            else if (mode == kAAOdd) batch_site<L, R, C, PHASE, true, kAAOdd>(a, idx);
-            else batch_site<L, R, C, PHASE, true, kAAEven>(a, idx);
-        } else {
-            if (mode == kPingPong) batch_site<L, R, C, PHASE, false, kPingPong>(a, idx);
-            else if (mode == kAAOdd) batch_site<L, R, C, PHASE, false, kAAOdd>(a, idx);
-            else batch_site<L, R, C, PHASE, false, kAAEven>(a, idx);
+        const bool masked = mem[j].has_mask != 0;
+        const long long base = (t - mem[j].first_item) * span * kSplitThreads + threadIdx.x;
+        for (int s = 0; s < span; ++s) {
+            const long long lidx = base + (long long)s * kSplitThreads;
+            if (lidx >= a.N) break;   // past the member's last site (so are the item's later blocks)
+            const int idx = (int)lidx;
+            if (masked) {
+                if (mode == kPingPong) batch_site<L, R, C, PHASE, true, kPingPong>(a, idx);
+                else if (mode == kAAOdd) batch_site<L, R, C, PHASE, true, kAAOdd>(a, idx);
+                else batch_site<L, R, C, PHASE, true, kAAEven>(a, idx);
+            } else {
+                if (mode == kPingPong) batch_site<L, R, C, PHASE, false, kPingPong>(a, idx);
+                else if (mode == kAAOdd) batch_site<L, R, C, PHASE, false, kAAOdd>(a, idx);
+                else batch_site<L, R, C, PHASE, false, kAAEven>(a, idx);
+            }
         }
     }
 }

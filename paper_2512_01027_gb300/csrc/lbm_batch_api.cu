@@ -116,8 +116,8 @@ int lbm_batch_create(int lattice, int storage, lbm_batch *out)
         return LBM_ERR_CUDA;
     }
     b->own_stream = true;
-    b->grid[0] = ops->batch_grid(0);
-    b->grid[1] = ops->batch_grid(1);
+    b->grid[0] = ops->batch_grid(0, 0);
+    b->grid[1] = ops->batch_grid(1, 0);
     *out = b;
     return LBM_OK;
 }
@@ -160,6 +160,22 @@ int lbm_batch_set_tuning(lbm_batch b, int chunk, int use_graph)
         return bfail(b, LBM_ERR_INVALID_ARG, "chunk in 1..64, use_graph 0 or 1");
     b->chunk = chunk;
     b->use_graph = use_graph != 0;
+    return LBM_OK;
+}
+
+int lbm_batch_set_shape(lbm_batch b, int span, int blocks_per_sm)
+{
+    if (!b) return LBM_ERR_INVALID_ARG;
+    if (span < 1 || span > kBatchMaxSpan || blocks_per_sm < 0 || blocks_per_sm > 32)
+        return bfail(b, LBM_ERR_INVALID_ARG, "span in 1..16, blocks_per_sm in 0..32");
+    cudaStreamSynchronize(b->stream);
+    b->span = span;
+    if (blocks_per_sm != b->blocks_per_sm) {
+        b->blocks_per_sm = blocks_per_sm;
+        b->grid[0] = b->ops->batch_grid(0, blocks_per_sm);
+        b->grid[1] = b->ops->batch_grid(1, blocks_per_sm);
+        drop_graphs(b);   // the captured launches carry the grid
+    }
     return LBM_OK;
 }
 
@@ -229,12 +245,13 @@ int lbm_batch_step(lbm_batch b, int64_t n, int *finished)
         BatchHeader hdr;
         std::memset(&hdr, 0, sizeof hdr);
         hdr.nmem = (long long)order.size();
+        hdr.span = b->span;
         char *mem = static_cast<char *>(b->h_table) + batch_header_bytes();
         long long first = 0;
         for (size_t r = 0; r < order.size(); ++r) {
             const lbm_ctx *h = b->members[order[r]];
             b->ops->batch_fill(h, take[order[r]], first, mem + r * mbytes);
-            const long long items = b->ops->batch_items(h);
+            const long long items = b->ops->batch_items(h, b->span);
             for (int k = 0; k < take[order[r]]; ++k) hdr.active[k] += items;
             first += items;
         }
@@ -298,6 +315,96 @@ const char *lbm_batch_last_error(lbm_batch b)
 
 // ---------------------------------------------------------------------------
 
+int lbm_batch_autotune(lbm_batch b, int trial_steps, int *chunk, int *span, int *blocks_per_sm, double *ms_per_step)
+{
+    if (!b) return LBM_ERR_INVALID_ARG;
+    if (trial_steps < 1 || trial_steps > 1000) return bfail(b, LBM_ERR_INVALID_ARG, "trial_steps in 1..1000");
+    if (b->members.empty()) return bfail(b, LBM_ERR_INVALID_ARG, "the batch has no members");
+    // every member's state and budget, restored after the trials
+    std::vector<std::vector<char>> saved(b->members.size());
+    std::vector<int64_t> budget = b->remaining;
+    int rc = LBM_OK;
+    for (size_t j = 0; j < b->members.size() && rc == LBM_OK; ++j) {
+        size_t bytes = 0;
+        rc = lbm_state_bytes(b->members[j], &bytes);
+        if (rc == LBM_OK) {
+            saved[j].resize(bytes);
+            rc = lbm_save_state(b->members[j], saved[j].data(), bytes);
+        }
+    }
+    if (rc != LBM_OK) return bfail(b, rc, "saving a member's state failed");
+    const int chunk0 = b->chunk, span0 = b->span, bps0 = b->blocks_per_sm;
+    int occ = 0;
+    {
+        int sms = 1;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+        occ = b->ops->batch_grid(0, 0) / (sms > 0 ? sms : 1);
+    }
+    struct Cand {
+        int chunk, span, bps;
+    };
+    std::vector<Cand> cands;
+    for (int K : {8, 16, 32})
+        for (int sp : {1, 2, 4, 8})
+            for (int bps : {0, occ > 2 ? occ - 1 : 0}) {
+                if (bps != 0 && bps == occ) continue;
+                bool dup = false;
+                for (const Cand &c : cands) dup = dup || (c.chunk == K && c.span == sp && c.bps == bps);
+                if (!dup) cands.push_back({K, sp, bps});
+            }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 1e300;
+    Cand pick{chunk0, span0, bps0};
+    for (const Cand &c : cands) {
+        rc = lbm_batch_set_shape(b, c.span, c.bps);
+        if (rc == LBM_OK) rc = lbm_batch_set_tuning(b, c.chunk, b->use_graph ? 1 : 0);
+        for (size_t j = 0; j < b->members.size(); ++j) b->remaining[j] = 1 << 30;
+        if (rc == LBM_OK) rc = lbm_batch_step(b, c.chunk, nullptr);   // warm-up: graph capture
+        if (rc != LBM_OK) break;
+        cudaEventRecord(e0, b->stream);
+        const int steps = (trial_steps + c.chunk - 1) / c.chunk * c.chunk;
+        rc = lbm_batch_step(b, steps, nullptr);
+        cudaEventRecord(e1, b->stream);
+        if (rc != LBM_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = bcuda(b, cudaGetLastError(), "batch autotune timing");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = ms / steps;
+        if (per < best) {
+            best = per;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // the members continue from their saved states, with their budgets
+    int rc_restore = LBM_OK;
+    for (size_t j = 0; j < b->members.size(); ++j) {
+        const int r = lbm_load_state(b->members[j], saved[j].data(), saved[j].size());
+        if (r != LBM_OK && rc_restore == LBM_OK) rc_restore = r;
+    }
+    b->remaining = budget;
+    if (rc != LBM_OK) {
+        lbm_batch_set_shape(b, span0, bps0);
+        lbm_batch_set_tuning(b, chunk0, b->use_graph ? 1 : 0);
+        return rc;
+    }
+    if (rc_restore != LBM_OK) return bfail(b, rc_restore, "restoring a member's state failed");
+    rc = lbm_batch_set_shape(b, pick.span, pick.bps);
+    if (rc == LBM_OK) rc = lbm_batch_set_tuning(b, pick.chunk, b->use_graph ? 1 : 0);
+    if (rc != LBM_OK) return rc;
+    if (chunk) *chunk = pick.chunk;
+    if (span) *span = pick.span;
+    if (blocks_per_sm) *blocks_per_sm = pick.bps;
+    if (ms_per_step) *ms_per_step = best;
+    return LBM_OK;
+}
+
 int lbm_autotune(lbm_handle h, int trial_steps, int *variant, int *zchunk, double *ms_per_step)
 {
     if (!h) return LBM_ERR_INVALID_ARG;
@@ -310,18 +417,24 @@ int lbm_autotune(lbm_handle h, int trial_steps, int *variant, int *zchunk, doubl
         return LBM_ERR_INVALID_ARG;
     }
     struct Cand {
-        int variant, zchunk;
+        int variant, zchunk, rows, staged;
     };
     std::vector<Cand> cands;
-    cands.push_back({3, 0});
-    if (h->ops->persist_ok(h)) cands.push_back({4, 0});
+    cands.push_back({3, 0, 0, -1});
+    if (h->ops->persist_ok(h)) cands.push_back({4, 0, 0, -1});
     if (!h->inplace) {
-        cands.push_back({1, 0});
+        cands.push_back({1, 0, 0, -1});
         if (h->ops->has_v2() && h->D == 3)
             for (int zc : {0, 4, 8, 16, 32, 64})
-                if (zc <= h->nz) cands.push_back({2, zc});
+                if (zc <= h->nz) cands.push_back({2, zc, 0, -1});
+        if (!h->consts.coupling)
+            for (int rows : {4, 8, 16})
+                if (h->ops->cluster_ok(h, rows))
+                    for (int st : {0, 1})
+                        for (int zc : {0, 64})
+                            if (zc <= h->nz) cands.push_back({5, zc, rows, st});
     }
-    const int v0 = h->variant, z0 = h->zchunk;
+    const int v0 = h->variant, z0 = h->zchunk, r0 = h->cluster_rows, s0 = h->cluster_stage;
     if (cands.size() == 1) {
         h->variant = cands[0].variant;
         if (variant) *variant = cands[0].variant;
@@ -340,6 +453,14 @@ int lbm_autotune(lbm_handle h, int trial_steps, int *variant, int *zchunk, doubl
     double best = 1e300;
     Cand pick = cands[0];
     for (const Cand &c : cands) {
+        if (c.variant == 5) {
+            rc = lbm_set_cluster(h, c.rows, c.staged);
+            if (rc == LBM_ERR_UNSUPPORTED) {   // e.g. clusters of 16 not allowed on the device
+                rc = LBM_OK;
+                continue;
+            }
+            if (rc != LBM_OK) break;
+        }
         rc = lbm_set_tuning(h, c.variant, c.zchunk);
         if (rc != LBM_OK) break;
         rc = h->ops->step(h, 1);   // warm-up (and first-use attributes)
@@ -366,10 +487,13 @@ int lbm_autotune(lbm_handle h, int trial_steps, int *variant, int *zchunk, doubl
     if (rc != LBM_OK) {
         h->variant = v0;
         h->zchunk = z0;
+        h->cluster_rows = r0;
+        h->cluster_stage = s0;
         return rc;
     }
     if (rc_restore != LBM_OK) return rc_restore;
-    rc = lbm_set_tuning(h, pick.variant, pick.zchunk);
+    if (pick.variant == 5) rc = lbm_set_cluster(h, pick.rows, pick.staged);
+    if (rc == LBM_OK) rc = lbm_set_tuning(h, pick.variant, pick.zchunk);
     if (rc != LBM_OK) return rc;
     if (variant) *variant = pick.variant;
     if (zchunk) *zchunk = pick.zchunk;

@@ -11,6 +11,7 @@
 #include "lbm_split.cuh"
 #include "lbm_batch.cuh"
 #include "lbm_persist.cuh"
+#include "lbm_cluster.cuh"
 
 #include <type_traits>
 
@@ -27,7 +28,7 @@ inline SiteConsts<R> site_consts(const HostConsts &h)
     k.invW = R(1.0 / h.W); k.invD = R(1.0 / h.D);
     k.A_mu = R(h.A_mu); k.B_mu = R(h.B_mu);
     k.g[0] = R(h.g[0]); k.g[1] = R(h.g[1]); k.g[2] = R(h.g[2]);
-    k.clamp = h.clamp; k.full_trace = h.full_trace;
+    k.clamp = h.clamp; k.full_trace = h.full_trace; k.coupling = h.coupling;
     return k;
 }
 
@@ -231,7 +232,12 @@ struct Impl {
     // --- batched persistent launch (lbm_batch_*) ---------------------------
     static size_t batch_member_bytes() { return sizeof(BatchMember<R, S>); }
 
-    static long long batch_items(const lbm_ctx *c) { return (c->N + kSplitThreads - 1) / kSplitThreads; }
+    // Work items of a member: `span` consecutive blocks of kSplitThreads sites.
+    static long long batch_items(const lbm_ctx *c, int span)
+    {
+        const long long per = (long long)kSplitThreads * span;
+        return (c->N + per - 1) / per;
+    }
 
     static void batch_fill(const lbm_ctx *c, int take, long long first_item, void *dst)
     {
@@ -242,13 +248,15 @@ struct Impl {
         m.mode[0] = split_mode(c, c->steps);
         m.mode[1] = split_mode(c, c->steps + 1);
         m.first_item = first_item;
-        m.items = batch_items(c);
+        m.items = batch_items(c, 1);
         m.take = take;
         m.has_mask = c->has_mask ? 1 : 0;
         std::memcpy(dst, &m, sizeof m);
     }
 
-    static int batch_grid(int phase)
+    // Persistent grid of a batch launch: blocks_per_sm per SM (0: as many as
+    // fit, the kernel's occupancy), never more than fit.
+    static int batch_grid(int phase, int blocks_per_sm)
     {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
@@ -257,7 +265,9 @@ struct Impl {
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<L, R, C, 0>, kSplitThreads, 0);
         else
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<L, R, C, 1>, kSplitThreads, 0);
-        return (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+        if (per_sm < 1) per_sm = 1;
+        if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
+        return per_sm * (sms > 0 ? sms : 1);
     }
 
     static cudaError_t batch_launch(cudaStream_t s, const void *d_table, int K, int grid0, int grid1)
@@ -339,10 +349,146 @@ struct Impl {
         return LBM_OK;
     }
 
+    // --- cluster step (one launch per step, variant 5) -------------------------
+    static bool cluster_ok_rows(const lbm_ctx *c, int cy)
+    {
+        if constexpr (L::D == 3 && !C::kGodd) return cluster_ok(L::D, L::Q, c->nx, c->ny, c->N, cy, c->inplace, false);
+        else return false;
+    }
+
+    // Rows per cluster: the handle's choice, else the largest of 16 (where
+    // the device allows that non-portable size), 8, 4, 2 the lattice fits.
+    static int cluster_rows(const lbm_ctx *c)
+    {
+        if (c->cluster_rows > 0) return c->cluster_rows;
+        if (cluster_ok_rows(c, 16) && cluster16_allowed(c)) return 16;
+        for (int r : {8, 4, 2})
+            if (cluster_ok_rows(c, r)) return r;
+        return 8;
+    }
+
+    static bool cluster16_allowed(const lbm_ctx *c)
+    {
+        if constexpr (L::D == 3 && !C::kGodd) {
+            static int ok = -1;
+            if (ok < 0) {
+                ok = 1;
+                for_each_cluster_kernel([&](auto kernel) {
+                    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+                        ok = 0;
+                });
+                cudaGetLastError();
+            }
+            (void)c;
+            return ok == 1;
+        } else {
+            (void)c;
+            return false;
+        }
+    }
+
+    // Every instantiation of the cluster kernel this (lattice, storage) has.
+    template <class F>
+    static void for_each_cluster_kernel(F &&f)
+    {
+        if constexpr (L::D == 3 && !C::kGodd) {
+            f(cluster_step_kernel<L, R, C, true, false>);
+            f(cluster_step_kernel<L, R, C, false, false>);
+            if constexpr (kPacked<R>) {
+                f(cluster_step_kernel<L, R, C, true, true>);
+                f(cluster_step_kernel<L, R, C, false, true>);
+            }
+        }
+    }
+
+    // Rows staged by bulk copies: FP32 arithmetic, unless the handle says no.
+    static bool cluster_staged(const lbm_ctx *c) { return kPacked<R> && c->cluster_stage != 0; }
+
+    static bool cluster_ok_h(const lbm_ctx *c) { return cluster_ok_rows(c, cluster_rows(c)); }
+
+    // Planes per CTA: the handle's zchunk when set, else about six waves of
+    // CTAs (two resident per SM).
+    static int cluster_zchunk(const lbm_ctx *c)
+    {
+        if (c->cluster_zchunk > 0) return c->cluster_zchunk < c->nz ? c->cluster_zchunk : c->nz;
+        int sms = 152;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+        const long long want = 6LL * 2 * sms;
+        long long chunks = (want + c->ny - 1) / c->ny;
+        if (chunks < 1) chunks = 1;
+        long long zc = (c->nz + chunks - 1) / chunks;
+        if (zc < 8) zc = 8;
+        if (zc > c->nz) zc = c->nz;
+        return (int)zc;
+    }
+
+    template <bool M, bool STAGE>
+    static int launch_cluster(lbm_ctx *c, const SplitArgs<R, S> &a)
+    {
+        if constexpr (L::D == 3 && !C::kGodd && (!STAGE || kPacked<R>)) {
+            const int cy = cluster_rows(c);
+            const size_t smem = cluster_smem_bytes<R, S>(c->nx, L::Q, STAGE);
+            static bool attr_set = false;
+            if (!attr_set) {
+                // the largest any lattice needs (nx = 256), set once
+                cudaError_t e = cudaFuncSetAttribute(
+                    cluster_step_kernel<L, R, C, M, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                    (int)cluster_smem_bytes<R, S>(kClusterMaxThreads, L::Q, STAGE));
+                if (e != cudaSuccess) return cuda_fail(c, e, "cudaFuncSetAttribute(cluster step)");
+                attr_set = true;
+            }
+            if (cy > 8) cluster16_allowed(c);
+            ClusterArgs g;
+            g.zchunk = cluster_zchunk(c);
+            g.cy = cy;
+            g.zper = c->periodic[2];
+            g.yper = c->periodic[1];
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(1, (unsigned)c->ny, (unsigned)((c->nz + g.zchunk - 1) / g.zchunk));
+            cfg.blockDim = dim3((unsigned)c->nx, 1, 1);
+            cfg.dynamicSmemBytes = smem;
+            cfg.stream = c->stream;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = 1;
+            attr[0].val.clusterDim.y = (unsigned)cy;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            return cuda_fail(c, cudaLaunchKernelEx(&cfg, cluster_step_kernel<L, R, C, M, STAGE>, a, g),
+                             "cluster_step_kernel launch");
+        } else {
+            (void)a;
+            c->err = "cluster step not available for this lattice/storage";
+            return LBM_ERR_UNSUPPORTED;
+        }
+    }
+
+    static int step_cluster(lbm_ctx *c, int64_t n)
+    {
+        if (n > 0) {
+            const int rc = split_prepare(c);
+            if (rc != LBM_OK) return rc;
+        }
+        for (int64_t s = 0; s < n; ++s) {
+            const SplitArgs<R, S> a = split_args(c, 0);
+            const bool st = cluster_staged(c);
+            const int rc = c->has_mask ? (st ? launch_cluster<true, true>(c, a) : launch_cluster<true, false>(c, a))
+                                       : (st ? launch_cluster<false, true>(c, a) : launch_cluster<false, false>(c, a));
+            if (rc != LBM_OK) return rc;
+            c->cur = 1 - c->cur;
+            c->steps += 1;
+            if constexpr (kPacked<R>) c->soa_valid = false;
+        }
+        return LBM_OK;
+    }
+
     static int step(lbm_ctx *c, int64_t n)
     {
+        if (c->variant == 5 && cluster_ok_h(c)) return step_cluster(c, n);
         if (c->variant == 4 && persist_ok(c)) return step_persist(c, n);
-        if (c->inplace || c->variant == 3 || c->variant == 0 || c->variant == 4) return step_split(c, n);
+        if (c->inplace || c->variant == 3 || c->variant == 0 || c->variant == 4 || c->variant == 5)
+            return step_split(c, n);
         if (n > 0) {
             int rc = sync_soa(c);
             if (rc == LBM_OK) rc = fold(c);
@@ -479,7 +625,7 @@ struct Impl {
         static const Ops o = {&init,      &step,       &read,         &reduce,      &pjump,
                               &probe,     &step_smem,  &has_v2,       &pack,        &sync_soa,
                               &persist_ok, &split_prepare, &fold, &batch_member_bytes,
-                              &batch_items, &batch_fill, &batch_grid, &batch_launch};
+                              &batch_items, &batch_fill, &batch_grid, &batch_launch, &cluster_ok_rows};
         return &o;
     }
 };

@@ -18,7 +18,7 @@ struct Ops;
 struct HostConsts {
     double rho_a, drho, om1, rhoref_T, cP, tau_a, dtau, inv_tau_phi, lambda_b, M3, W, eps, phi_n, phi_m, D,
         dt_pref, A_mu, B_mu, g[3];
-    int clamp, full_trace;
+    int clamp, full_trace, coupling;
 };
 
 HostConsts make_consts(const lbm_params &p);
@@ -35,8 +35,11 @@ constexpr int kBatchMaxChunk = 64;
 
 struct BatchHeader {
     long long nmem;
+    long long span;                       // consecutive 128-site blocks per work item
     long long active[kBatchMaxChunk];
 };
+
+constexpr int kBatchMaxSpan = 16;
 
 constexpr size_t batch_header_bytes() { return (sizeof(BatchHeader) + 255) / 256 * 256; }
 
@@ -80,6 +83,9 @@ struct lbm_ctx {
     int zchunk = 64;
     int zchunk_auto = 64;
     int variant = 0;
+    int cluster_rows = 0;          // CTAs (rows) per cluster of the cluster step (0: automatic)
+    int cluster_zchunk = 0;        // planes per CTA of the cluster step (0: automatic)
+    int cluster_stage = 1;         // cluster step with FP32 arithmetic: rows staged by bulk copies (0: off)
     cudaStream_t stream = nullptr;
     int64_t steps = 0;
     std::string err;
@@ -105,6 +111,8 @@ struct lbm_batch_ctx {
     void *h_table = nullptr;          // pinned staging copy
     std::vector<std::pair<int, cudaGraphExec_t>> graphs;   // per chunk length
     int grid[2] = {0, 0};
+    int span = 1;                     // 128-site blocks per work item
+    int blocks_per_sm = 0;            // persistent blocks per SM (0: the kernels' occupancy)
     int64_t launches = 0;             // kernels launched so far
     std::string err;
 };
@@ -128,10 +136,12 @@ struct Ops {
     int (*fold)(lbm_ctx *c);                // g* complete in the store again (BF16 storage)
     // batched persistent launch (lbm_batch_*)
     size_t (*batch_member_bytes)();
-    long long (*batch_items)(const lbm_ctx *c);
+    long long (*batch_items)(const lbm_ctx *c, int span);
     void (*batch_fill)(const lbm_ctx *c, int take, long long first_item, void *dst);
-    int (*batch_grid)(int phase);
+    int (*batch_grid)(int phase, int blocks_per_sm);
     cudaError_t (*batch_launch)(cudaStream_t s, const void *d_table, int K, int grid0, int grid1);
+    // cluster step (variant 5) with `rows` CTAs per cluster
+    bool (*cluster_ok)(const lbm_ctx *c, int rows);
 };
 
 // One instantiation per (storage, lattice); lattice 0 D2Q9, 1 D3Q19, 2 D3Q27.

@@ -1,18 +1,20 @@
 // Allocation-free variant of the FP64 field reduction (lbm_reduce_fields_noalloc).
 //
 // Some callers cannot allocate device memory at the point where they need a
-// reduction: work recorded while a CUDA stream is being captured into a graph
-// (cudaMalloc is not a capturable operation), real-time loops that must not
-// block in an allocator, and hosts whose device memory comes from a pool they
-// do not own.  This entry point takes its inputs and its output from the
-// caller and keeps the per-block partial sums in a fixed array in device
-// global memory instead of allocating them.
+// reduction: real-time loops that must not block in an allocator (cudaMalloc
+// and cudaFree can synchronise the device), and hosts whose device memory
+// comes from a pool they do not own, where a library allocating on its own
+// would break the host's accounting.  This entry point takes its inputs and
+// its output from the caller and keeps the per-block partial sums in a fixed
+// array in device global memory instead of allocating them.
 //
 // The array below is a file-scope __device__ variable: every GPU that loads
 // this library holds it (40 KB) until the process exits.  In host code its name
 // is only a host-side stand-in, not a device address; the device address is
 // obtained per device with cudaGetSymbolAddress on the first call made with
-// that device current, and cached.
+// that device current (so that first call should come before any stream
+// capture), and cached for as long as the device's context lives: after a
+// cudaDeviceReset the library has to be loaded again.
 #include <mutex>
 
 #include "lbm_internal.h"
@@ -91,8 +93,13 @@ extern "C" int lbm_reduce_fields_noalloc(const double *d_phi, const double *d_u,
     const int blocks = (int)std::min<long long>(kStaticBlocks, (n + kRedThreads - 1) / kRedThreads);
     // every block writes its own partial vector before the second pass reads
     // exactly `blocks` of them, so nothing in the array needs clearing
+    // Launch errors are read with cudaPeekAtLastError, which leaves the
+    // thread's error state as it is: an error already pending from earlier
+    // work also makes this call return LBM_ERR_CUDA, and stays pending for
+    // the caller's own checks.
     field_sums_kernel<<<blocks, kRedThreads, 0, s>>>(d_phi, d_u, d_solid, (long long)n, rho_a, rho_w - rho_a,
                                                      clamp_phi_props ? 1 : 0, partials);
+    if (cudaPeekAtLastError() != cudaSuccess) return LBM_ERR_CUDA;
     finish_kernel<kRedVals><<<1, kRedThreads, 0, s>>>(partials, blocks, d_out);
-    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+    return cudaPeekAtLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }

@@ -40,6 +40,7 @@ struct SiteConsts {
     R g[3];         // body acceleration
     int clamp;
     int full_trace;
+    int coupling;   // 1: the omega-term of P takes u^{n+1} (added by the collision launch)
 };
 
 template <class R>
@@ -339,13 +340,36 @@ __host__ __device__ constexpr int pig_slot(int a, int b)
     return D == 3 ? (a == 0 ? b : (a == 1 ? 2 + b : 5)) : (a == 0 ? b : 2);
 }
 
+// Knuth's TwoSum: s = RN(a + b) and the exact rounding error e, s + e = a + b
+// (round-to-nearest intrinsics, so nothing is contracted or reassociated).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Unbiased rounding of the pair value hi + lo (|lo| at most half an ulp of
+// hi) to a float: hi, or its neighbour on the side of lo with probability
+// |lo| / (the gap to it), decided by the uniform 32 bits r.
+__device__ __forceinline__ float round_pair_sr(float hi, float lo, uint32_t r)
+{
+    if (lo == 0.f) return hi;
+    const float nb = nextafterf(hi, lo > 0.f ? INFINITY : -INFINITY);
+    const float p = fabsf(lo) / fabsf(__fsub_rn(nb, hi));
+    return (float)(r >> 8) * (1.0f / 16777216.0f) < p ? nb : hi;
+}
+
 // GODD: g* is returned without its odd first-order part w_i c_i . V_g, and
 // V_g = u/T + F/(rho T) + sigma grad rho/(rho^2 T) is returned in vgout.
-template <class L, bool INIT, bool PDEV, bool GMOM = false, bool GODD = false>
+// EXACT0: the rest population closes the phase mass from exact sums (see
+// below), rounded without bias by the uniform bits rbits.
+template <class L, bool INIT, bool PDEV, bool GMOM = false, bool GODD = false, bool EXACT0 = false>
 __device__ __forceinline__ void collide_pairs(const SiteConsts<float> &k, float phi, float phihat, float rho,
                                               float P, const float (&u)[3], const float (&gphi)[3], float lphi,
                                               const float (&gu)[3][3], const float *hp, const float *gp, float *hs,
-                                              float *gs, const float *pig = nullptr, float *vgout = nullptr)
+                                              float *gs, const float *pig = nullptr, float *vgout = nullptr,
+                                              uint32_t rbits = 0u)
 {
     constexpr int D = L::D;
     constexpr int NP = (L::Q - 1) / 2;
@@ -412,11 +436,21 @@ __device__ __forceinline__ void collide_pairs(const SiteConsts<float> &k, float 
     const float kF = 3.f * rinv;          // 1 / (rho T)
     const float kS = kF * rinv;           // 1 / (rho^2 T)
     const float bdiv = B * div * 3.f;     // B div / T
+    // D2Q9: the odd part of g_eq, w_i c_i . (u/T + F/(rho T) + ...), with one
+    // rounding in place of three.  Formed as 3 c.u + c.V_f in one float, the
+    // body force of a slow steady flow (1e-7 against u/T ~ 0.3) loses a few
+    // per cent at every step in the same direction, and the velocity drifts
+    // by 1e-5 of itself in 1000 steps; kept exact as a float pair (an FMA
+    // for the product by 3, TwoSum for the sum, w_i as a float pair) it is
+    // rounded once, and the drift stays at the level of the storage.
+    constexpr bool kCompOdd = L::Q == 9;
     float Vh[3], Vg[3];
+    [[maybe_unused]] float Vf[3];
     static_for<0, 3>([&](auto A) {
         constexpr int a = decltype(A)::value;
         Vh[a] = 3.f * phi * u[a] + theta_tot * n[a];
         Vg[a] = 3.f * u[a] + F[a] * kF + sg[a] * kS;
+        if constexpr (kCompOdd) Vf[a] = F[a] * kF + sg[a] * kS;
     });
     if constexpr (GODD) {
         vgout[0] = Vg[0];
@@ -444,7 +478,18 @@ __device__ __forceinline__ void collide_pairs(const SiteConsts<float> &k, float 
         const float oh = wi * dot_c<L, i>(Vh);
         seh = __fadd_rn(seh, eh);                    // no contraction: every kernel rounds eh alike
         eg[p] = wi * (Eg0 + 4.5f * cu2);
-        og[p] = wi * dot_c<L, i>(Vg);
+        if constexpr (kCompOdd) {
+            constexpr float whi = float(L::w(i));
+            constexpr float wlo = float(L::w(i) - double(whi));
+            const float p3 = __fmul_rn(3.f, cu);
+            const float e1 = fmaf(3.f, cu, -p3);              // 3 c.u = p3 + e1 exactly
+            float sv, e2;
+            two_sum(p3, dot_c<L, i>(Vf), sv, e2);
+            const float lo = __fadd_rn(e1, e2);
+            og[p] = fmaf(whi, sv, fmaf(whi, lo, __fmul_rn(wlo, sv)));
+        } else {
+            og[p] = wi * dot_c<L, i>(Vg);
+        }
         if constexpr (INIT) {
             hs[i] = eh + oh;
             hs[i + 1] = eh - oh;
@@ -471,9 +516,32 @@ __device__ __forceinline__ void collide_pairs(const SiteConsts<float> &k, float 
         // pulled h: the rounding of the moving populations then does not
         // accumulate in the phase mass.  In exact arithmetic this is
         // h_0 - (h_0 - h_eq_0) / tau_phi.
-        float sm = 0.f;
-        static_for<1, L::Q>([&](auto I) { sm = __fadd_rn(sm, hs[decltype(I)::value]); });
-        hs[0] = __fsub_rn(phi, sm);
+        if constexpr (EXACT0) {
+            // The same closure with the sum of the pulled h and the sum of
+            // the moving h* kept exactly as (hi, lo) pairs and the result
+            // rounded without bias: the rounding of the sums no longer leans
+            // the same way step after step at a site of a slow flow, so the
+            // phase mass does not drift (the FP32 sums alone leave 2.8e-5
+            // over 20000 steps of the 2D rising bubble).
+            float ps = hp[0], pc = 0.f, ss = hs[1], sc = 0.f, e;
+            static_for<1, L::Q>([&](auto I) {
+                two_sum(ps, hp[decltype(I)::value], ps, e);
+                pc = __fadd_rn(pc, e);
+            });
+            static_for<2, L::Q>([&](auto I) {
+                two_sum(ss, hs[decltype(I)::value], ss, e);
+                sc = __fadd_rn(sc, e);
+            });
+            float vh, vl;
+            two_sum(ps, -ss, vh, e);
+            vl = __fadd_rn(e, __fsub_rn(pc, sc));
+            two_sum(vh, vl, vh, vl);
+            hs[0] = round_pair_sr(vh, vl, rbits);
+        } else {
+            float sm = 0.f;
+            static_for<1, L::Q>([&](auto I) { sm = __fadd_rn(sm, hs[decltype(I)::value]); });
+            hs[0] = __fsub_rn(phi, sm);
+        }
     }
     if constexpr (!INIT) {
         // Pi_ab = sum_k c_ka c_kb (g_k - g_eq_k), per pair (c_ka c_kb is even in c)

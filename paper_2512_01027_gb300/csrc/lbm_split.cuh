@@ -120,6 +120,27 @@ inline constexpr bool kPacked = std::is_same<R, float>::value;
 constexpr int kSplitThreads = 128;
 constexpr int kSplitMinBlocks = 4;   // <= 128 registers a thread: 16 warps an SM
 
+// Source of the pulled populations of the moments: GlobalPull reads them
+// from the population store at read_idx (every stream mode, bounce-back
+// included); the cluster step substitutes rows it staged in shared memory.
+template <class L, int MODE, class IX, bool HAS_MASK, class S>
+struct GlobalPull {
+    const S *h, *g;
+    template <int i>
+    __device__ __forceinline__ void get(IX N, const Nbr32 &nb, int idx, uint32_t m, S &hr, S &gr) const
+    {
+        const IX e = read_idx<L, MODE, i, IX>(N, nb, idx, m, HAS_MASK);
+        hr = h[e];
+        gr = g[e];
+    }
+};
+
+template <class L, int MODE, class IX, bool HAS_MASK, class S>
+__device__ __forceinline__ GlobalPull<L, MODE, IX, HAS_MASK, S> global_pull(const S *h, const S *g)
+{
+    return GlobalPull<L, MODE, IX, HAS_MASK, S>{h, g};
+}
+
 // S0 + S1 at site idx with FP32 arithmetic.  Every pulled population and
 // every neighbour word goes straight into running sums, so no per-direction
 // value waits for phi: 1/(T rho) multiplies the pressure sums once, after the
@@ -127,9 +148,9 @@ constexpr int kSplitMinBlocks = 4;   // <= 128 registers a thread: 16 warps an S
 // g differences + 1/(T rho) sum w_i c_i {P(x - c_i) - P(x + c_i)} per pair),
 // accumulated as the loads arrive, which leaves registers for more loads in
 // flight.
-template <class L, class C, bool HAS_MASK, int MODE, class IX>
+template <class L, class C, bool HAS_MASK, int MODE, class IX, class Pull, class Sink>
 __device__ __forceinline__ void moments_site_packed(const SplitArgs<float, typename C::S> &a, const int idx,
-                                                    const uint32_t m)
+                                                    const uint32_t m, const Pull &pull, Sink &&sink)
 {
     constexpr int D = L::D, Q = L::Q;
     constexpr int NS = D == 3 ? 6 : 3;
@@ -147,9 +168,10 @@ __device__ __forceinline__ void moments_site_packed(const SplitArgs<float, typen
     float gfirst = 0.f, pfirst = 0.f;   // the first member (c) of the current pair (c, -c)
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        const IX e = read_idx<L, MODE, i, IX>(N, nb, idx, m, HAS_MASK);
-        const float hv = C::template dec_h<i>(a.src_h[e]);
-        float gv = C::template dec_g<i>(a.src_g[e]);
+        typename C::S hr, gr;
+        pull.template get<i>(N, nb, idx, m, hr, gr);
+        const float hv = C::template dec_h<i>(hr);
+        float gv = C::template dec_g<i>(gr);
         if constexpr (i == 0) {
             phi = hv;
             sumg = gv;
@@ -209,14 +231,10 @@ __device__ __forceinline__ void moments_site_packed(const SplitArgs<float, typen
         u[ax] = ug[ax] + kfac * up[ax];                  // u = sum_i (g_i + K_i) c_i
     });
     const float sumK = kfac * (swP - float(1.0 - L::w(0)) * P0);
-    const float Pnew = s1_pressure_pairs<float, C::kPdev>(a.k, rho, sumg, sumK, sum_wcu, P0);
+    // the u^{n+1} coupling leaves the omega-term to the collision launch
+    const float Pnew = s1_pressure_pairs<float, C::kPdev>(a.k, rho, sumg, sumK, a.k.coupling ? 0.f : sum_wcu, P0);
     const float uz = D == 3 ? u[2] : 0.f;
-    a.F_new[idx] = make_float4(u[0], u[1], uz, Pnew);
-    a.FB[idx] = make_float4(u[0], u[1], uz, phi);
-    static_for<0, NS>([&](auto J) {
-        constexpr int j = decltype(J)::value;
-        a.PiG[eidx<IX>(j, N, idx)] = pm[j];
-    });
+    sink(u[0], u[1], uz, Pnew, phi, pm);
 }
 
 // Separable neighbour sums (D3Q27).  Its weights factor over the axes,
@@ -294,8 +312,9 @@ __device__ __forceinline__ float lane_xp(float v, float h, int lane)
 //   sum_i w_i c_ia P(x - c_i)    = - D_a S S P
 //   sum_i w_i c_i . u(x - c_i)   = - sum_a D_a S S u_a
 // the same quantities moments_site_packed sums direction by direction.
-template <class L, class C, int MODE, class IX>
-__device__ __forceinline__ void moments_site_sep(const SplitArgs<float, typename C::S> &a, const int idx)
+template <class L, class C, int MODE, class IX, class Pull, class Sink>
+__device__ __forceinline__ void moments_site_sep(const SplitArgs<float, typename C::S> &a, const int idx,
+                                                 const Pull &pull, Sink &&sink)
 {
     static_assert(L::Q == 27 && !C::kGodd, "separable moments: D3Q27 without the odd-part deferral");
     constexpr int Q = L::Q, NS = 6;
@@ -312,9 +331,10 @@ __device__ __forceinline__ void moments_site_sep(const SplitArgs<float, typename
     float gfirst = 0.f;
     static_for<0, Q>([&](auto I) {
         constexpr int i = decltype(I)::value;
-        const IX e = read_idx<L, MODE, i, IX>(N, nb, idx, 0u, false);
-        const float hv = C::template dec_h<i>(a.src_h[e]);
-        const float gv = C::template dec_g<i>(a.src_g[e]);
+        typename C::S hr, gr;
+        pull.template get<i>(N, nb, idx, 0u, hr, gr);
+        const float hv = C::template dec_h<i>(hr);
+        const float gv = C::template dec_g<i>(gr);
         if constexpr (i == 0) {
             phi = hv;
             sumg = gv;
@@ -352,7 +372,7 @@ __device__ __forceinline__ void moments_site_sep(const SplitArgs<float, typename
     up[2] = -sm3(lane_xm(own.dzP, hal.dzP, lane), own.dzP, lane_xp(own.dzP, hal.dzP, lane));
     const float divu = df3(lane_xm(own.sUx, hal.sUx, lane), lane_xp(own.sUx, hal.sUx, lane)) +
                        sm3(lane_xm(own.e, hal.e, lane), own.e, lane_xp(own.e, hal.e, lane));
-    const float sum_wcu = -divu;
+    const float sum_wcu = a.k.coupling ? 0.f : -divu;   // the u^{n+1} coupling: added by the collision
     const float swP = sssP - float(L::w(0)) * P0;
     const float phihat = a.k.clamp ? clamp01(phi) : phi;
     const float rho = a.k.rho_a + phihat * a.k.drho;
@@ -364,12 +384,7 @@ __device__ __forceinline__ void moments_site_sep(const SplitArgs<float, typename
     });
     const float sumK = kfac * (swP - float(1.0 - L::w(0)) * P0);
     const float Pnew = s1_pressure_pairs<float, C::kPdev>(a.k, rho, sumg, sumK, sum_wcu, P0);
-    a.F_new[idx] = make_float4(u[0], u[1], u[2], Pnew);
-    a.FB[idx] = make_float4(u[0], u[1], u[2], phi);
-    static_for<0, NS>([&](auto J) {
-        constexpr int j = decltype(J)::value;
-        a.PiG[eidx<IX>(j, N, idx)] = pm[j];
-    });
+    sink(u[0], u[1], u[2], Pnew, phi, pm);
 }
 
 // True when the separable form applies to this kernel instantiation (its
@@ -377,65 +392,105 @@ __device__ __forceinline__ void moments_site_sep(const SplitArgs<float, typename
 template <class L, class R, class C>
 inline constexpr bool kSepForm = kPacked<R> && L::Q == 27 && !C::kGodd;
 
+// The split form's hand-over of the moments (FP32 arithmetic): the packed
+// (u^{n+1}, P^{n+1}) state word, the packed (u^{n+1}, phi^{n+1}) word and
+// the second moments of the pulled g.
+template <class L, class C, class IX>
+__device__ __forceinline__ auto split_sink(const SplitArgs<float, typename C::S> &a, const int idx)
+{
+    return [&a, idx](float ux, float uy, float uz, float Pnew, float phi, const float *pm) {
+        constexpr int NS = L::D == 3 ? 6 : 3;
+        a.F_new[idx] = make_float4(ux, uy, uz, Pnew);
+        a.FB[idx] = make_float4(ux, uy, uz, phi);
+        static_for<0, NS>([&](auto J) {
+            constexpr int j = decltype(J)::value;
+            a.PiG[eidx<IX>(j, (IX)a.N, idx)] = pm[j];
+        });
+    };
+}
+
+// S0 + S1 at site idx with FP32 arithmetic, results to sink(u_x, u_y, u_z,
+// P^{n+1}, phi^{n+1}, pm).  With nx a multiple of 32 every warp is 32
+// consecutive sites of one row, and a warp whose sites have no solid or
+// outside neighbour takes the separable sums, or at least the code without
+// bounce-back selections.  Every lane of the warp calls it (warp vote).
+template <class L, class C, bool HAS_MASK, int MODE, class IX, class Pull, class Sink>
+__device__ __forceinline__ void moments_site_f32(const SplitArgs<float, typename C::S> &a, const int idx,
+                                                 const uint32_t m, const Pull &pull, Sink &&sink)
+{
+    if ((a.nx & 31) == 0 && !(HAS_MASK && __any_sync(0xffffffffu, m != 0u))) {
+        if constexpr (kSepForm<L, float, C>) moments_site_sep<L, C, MODE, IX>(a, idx, pull, sink);
+        else moments_site_packed<L, C, false, MODE, IX>(a, idx, 0u, pull, sink);
+        return;
+    }
+    if (m & kSolidBit) return;
+    moments_site_packed<L, C, HAS_MASK, MODE, IX>(a, idx, m, pull, sink);
+}
+
+// S0 + S1 at a fluid site idx in the canonical order of the oracle (FP64),
+// results to sink(u, P^{n+1}, phi^{n+1}).
+template <class L, class R, class C, bool HAS_MASK, int MODE, class IX, class Sink>
+__device__ __forceinline__ void moments_site_canon(const SplitArgs<R, typename C::S> &a, const int idx,
+                                                   const uint32_t m, Sink &&sink)
+{
+    constexpr int D = L::D, Q = L::Q;
+    const IX N = (IX)a.N;
+    const Nbr32 nb(idx, a.nx, a.ny, D == 3 ? a.nz : 1);
+    R hp[Q], gp[Q], Pn[Q], K[Q];
+    const R P0 = a.P_old[idx];
+    R sum_wcu = R(0);
+    static_for<0, Q>([&](auto I) {
+        constexpr int i = decltype(I)::value;
+        const IX e = read_idx<L, MODE, i, IX>(N, nb, idx, m, HAS_MASK);
+        hp[i] = C::template dec_h<i>(a.src_h[e]);
+        gp[i] = C::template dec_g<i>(a.src_g[e]);
+        if constexpr (i == 0) {
+            Pn[0] = P0;
+        } else {
+            const bool bb = HAS_MASK && ((m >> i) & 1u);
+            const int src = nb.at<L, i>(-1);
+            R un[3];
+            Pn[i] = bb ? P0 : a.P_old[src];
+            static_for<0, 3>([&](auto A) {
+                constexpr int ax = decltype(A)::value;
+                if constexpr (ax < D && L::c(i, ax) != 0) {
+                    if (!bb) un[ax] = a.u_old[eidx<IX>(ax, N, src)];
+                } else {
+                    un[ax] = R(0);
+                }
+            });
+            if (!bb) sum_wcu = sum_wcu + R(L::w(i)) * dot_c<L, i>(un);
+        }
+    });
+    R phi, phihat, rho, u[3];
+    s1_moments<L, R>(a.k, hp, gp, Pn, P0, phi, phihat, rho, u, K);
+    // the u^{n+1} coupling: the collision launch adds the omega-term
+    const R Pnew = s1_pressure<L, R, C::kPdev>(a.k, gp, K, rho, a.k.coupling ? R(0) : sum_wcu, P0);
+    sink(u, Pnew, phi);
+}
+
 // S0 + S1 at site idx (0 <= idx < a.N).  FP64: the canonical order of the
-// oracle; FP32 arithmetic: moments_site_packed.
+// oracle; FP32 arithmetic: moments_site_f32 into the split form's hand-over.
 template <class L, class R, class C, bool HAS_MASK, int MODE, class IX>
 __device__ __forceinline__ void moments_site(const SplitArgs<R, typename C::S> &a, const int idx)
 {
-    constexpr int D = L::D, Q = L::Q;
+    constexpr int D = L::D;
     uint32_t m = 0;
     if constexpr (HAS_MASK) m = a.mask[idx];
     if constexpr (kPacked<R>) {
-        // nx a multiple of 32: every warp is 32 consecutive sites of one row,
-        // and a warp whose sites have no solid or outside neighbour takes the
-        // separable sums, or at least the code without bounce-back selections
-        if ((a.nx & 31) == 0 && !(HAS_MASK && __any_sync(0xffffffffu, m != 0u))) {
-            if constexpr (kSepForm<L, R, C>) moments_site_sep<L, C, MODE, IX>(a, idx);
-            else moments_site_packed<L, C, false, MODE, IX>(a, idx, 0u);
-            return;
-        }
-    }
-    if (m & kSolidBit) return;
-    if constexpr (kPacked<R>) {
-        moments_site_packed<L, C, HAS_MASK, MODE, IX>(a, idx, m);
+        moments_site_f32<L, C, HAS_MASK, MODE, IX>(a, idx, m, global_pull<L, MODE, IX, HAS_MASK>(a.src_h, a.src_g),
+                                                   split_sink<L, C, IX>(a, idx));
     } else {
-        const IX N = (IX)a.N;
-        const Nbr32 nb(idx, a.nx, a.ny, D == 3 ? a.nz : 1);
-        R hp[Q], gp[Q], Pn[Q], K[Q];
-        const R P0 = a.P_old[idx];
-        R sum_wcu = R(0);
-        static_for<0, Q>([&](auto I) {
-            constexpr int i = decltype(I)::value;
-            const IX e = read_idx<L, MODE, i, IX>(N, nb, idx, m, HAS_MASK);
-            hp[i] = C::template dec_h<i>(a.src_h[e]);
-            gp[i] = C::template dec_g<i>(a.src_g[e]);
-            if constexpr (i == 0) {
-                Pn[0] = P0;
-            } else {
-                const bool bb = HAS_MASK && ((m >> i) & 1u);
-                const int src = nb.at<L, i>(-1);
-                R un[3];
-                Pn[i] = bb ? P0 : a.P_old[src];
-                static_for<0, 3>([&](auto A) {
-                    constexpr int ax = decltype(A)::value;
-                    if constexpr (ax < D && L::c(i, ax) != 0) {
-                        if (!bb) un[ax] = a.u_old[eidx<IX>(ax, N, src)];
-                    } else {
-                        un[ax] = R(0);
-                    }
-                });
-                if (!bb) sum_wcu = sum_wcu + R(L::w(i)) * dot_c<L, i>(un);
-            }
+        if (m & kSolidBit) return;
+        moments_site_canon<L, R, C, HAS_MASK, MODE, IX>(a, idx, m, [&](const R (&u)[3], R Pnew, R phi) {
+            const IX N = (IX)a.N;
+            a.P_new[idx] = Pnew;
+            static_for<0, D>([&](auto A) {
+                constexpr int ax = decltype(A)::value;
+                a.u_new[eidx<IX>(ax, N, idx)] = u[ax];
+            });
+            a.phi[idx] = phi;
         });
-        R phi, phihat, rho, u[3];
-        s1_moments<L, R>(a.k, hp, gp, Pn, P0, phi, phihat, rho, u, K);
-        const R Pnew = s1_pressure<L, R, C::kPdev>(a.k, gp, K, rho, sum_wcu, P0);
-        a.P_new[idx] = Pnew;
-        static_for<0, D>([&](auto A) {
-            constexpr int ax = decltype(A)::value;
-            a.u_new[eidx<IX>(ax, N, idx)] = u[ax];
-        });
-        a.phi[idx] = phi;
     }
 }
 
@@ -510,6 +565,38 @@ __device__ __forceinline__ void collide_site_impl(const SplitArgs<R, typename C:
     }
     const R phihat = a.k.clamp ? clamp01(phi) : phi;
     const R rho = a.k.rho_a + phihat * a.k.drho;
+    if (a.k.coupling) {
+        // The alternative reading of the pressure formula: the omega-term
+        // omega rho_ref sum_i w_i c_i . u(x - c_i) with the new velocity,
+        // whose neighbours the moments launch did not have yet.
+        const R omega = (rho - a.k.rho_a) / a.k.drho * a.k.om1;
+        R swcu = R(0);
+        if constexpr (kPacked<R>) {
+            // sum_i w_i c_i . u(x - c_i) = -T div u with the pair stencil's
+            // divergence (the same wall rule: u = 0 at a solid neighbour)
+            R div = gu[0][0] + gu[1][1];
+            if constexpr (D == 3) div = div + gu[2][2];
+            swcu = div * R(-1.0 / 3.0);
+        } else {
+            // the canonical order of the moments' own sum
+            static_for<1, Q>([&](auto I) {
+                constexpr int i = decltype(I)::value;
+                if (!(HAS_MASK && ((m >> i) & 1u))) {
+                    const int src = nb.at<L, i>(-1);
+                    R un[3];
+                    static_for<0, 3>([&](auto A) {
+                        constexpr int ax = decltype(A)::value;
+                        if constexpr (ax < D && L::c(i, ax) != 0) un[ax] = a.u_new[eidx<IX>(ax, N, src)];
+                        else un[ax] = R(0);
+                    });
+                    swcu = swcu + R(L::w(i)) * dot_c<L, i>(un);
+                }
+            });
+        }
+        P = P + omega * a.k.rho_a * swcu;
+        if constexpr (kPacked<R>) a.F_new[idx].w = P;
+        else a.P_new[idx] = P;
+    }
     R hp[Q], hs[Q], gs[Q];
     if constexpr (kPacked<R>) {
         if constexpr (!kEarlyH) load_h_pig();
@@ -518,8 +605,13 @@ __device__ __forceinline__ void collide_site_impl(const SplitArgs<R, typename C:
             hp[i] = C::template dec_h<i>(hraw[i]);
         });
         float vg[3];
-        collide_pairs<L, false, C::kPdev, true, C::kGodd>(a.k, phi, phihat, rho, P, u, gphi, lphi, gu, hp, nullptr,
-                                                         hs, gs, pm, vg);
+        // D2Q9 with FP32 storage: the rest population's phase-mass closure
+        // from exact sums, rounded without bias (random bits of (site, step))
+        constexpr bool kExact0 = L::Q == 9 && !C::kRound16;
+        uint32_t rb = 0u;
+        if constexpr (kExact0) rb = mix32((uint32_t)idx * 0x9e3779b9u ^ mix32(a.seed));
+        collide_pairs<L, false, C::kPdev, true, C::kGodd, kExact0>(a.k, phi, phihat, rho, P, u, gphi, lphi, gu, hp,
+                                                                  nullptr, hs, gs, pm, vg, rb);
         if constexpr (C::kGodd) a.G_new[idx] = make_float4(vg[0], vg[1], vg[2], 0.f);
     } else {
         R gp[Q];

@@ -20,6 +20,12 @@ surface tension, number of steps).  The server
 Latency is arrival -> result on the host.  The per-site arithmetic of a
 batch does not depend on the other members, so a request's result is the
 same whether it is served alone or in any mix.
+
+A request whose solve produces a non-finite phi, P or u (the method itself
+diverges for some small, high-density-ratio droplets of the trace; the FP64
+oracle does too) is retired when its steps are done with ``failed`` set and
+no fields; the summary counts such requests apart and takes the latency
+percentiles over the completed ones.
 """
 from __future__ import annotations
 
@@ -30,7 +36,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import Batch, Lattice, estimate_footprint
+from . import LBM_ERR_NONFINITE, Batch, Lattice, LbmError, estimate_footprint
 
 
 @dataclass
@@ -42,6 +48,7 @@ class Served:
     steps: int
     sites: int
     fields: tuple | None = None
+    failed: bool = False
 
     @property
     def latency(self) -> float:
@@ -57,10 +64,13 @@ class ServeStats:
     launches: int = 0
 
     def summary(self) -> dict:
-        lat = np.array([r.latency for r in self.results]) if self.results else np.zeros(1)
+        done = [r for r in self.results if not r.failed]
+        lat = np.array([r.latency for r in done]) if done else np.zeros(1)
         sites = sum(r.sites * r.steps for r in self.results)
         return {
             "requests": len(self.results),
+            "failed": len(self.results) - len(done),
+            "failed_ids": [r.rid for r in self.results if r.failed],
             "solves_per_s": len(self.results) / self.makespan if self.makespan > 0 else 0.0,
             "mlups": sites / self.makespan / 1e6 if self.makespan > 0 else 0.0,
             "p50_s": float(np.percentile(lat, 50)),
@@ -156,14 +166,14 @@ class Server:
                 keep = []
                 for r, L, need, t_adm in active:
                     if self.batch.remaining(L) == 0:
-                        out = L.read_fields()
+                        out, failed = _read_result(L)
                         t_fin = clock() - t0
                         self.batch.remove(L)
                         L.close()
                         used -= need
                         sites -= L.N
                         stats.results.append(Served(r.rid, r.arrival, t_adm, t_fin, r.steps, L.N,
-                                                    out if self.keep_fields else None))
+                                                    out if self.keep_fields else None, failed))
                     else:
                         keep.append((r, L, need, t_adm))
                 active = keep
@@ -171,6 +181,16 @@ class Server:
         stats.launches = self.batch.info()[1] - launches0
         stats.results.sort(key=lambda s: s.rid)
         return stats
+
+
+def _read_result(L: Lattice):
+    """Fields of a finished lattice, or (None, True) when its solve diverged."""
+    try:
+        return L.read_fields(), False
+    except LbmError as e:
+        if e.code != LBM_ERR_NONFINITE:
+            raise
+        return None, True
 
 
 def run_one_at_a_time(requests, storage: str = "f32", clock=time.perf_counter) -> ServeStats:
@@ -189,10 +209,10 @@ def run_one_at_a_time(requests, storage: str = "f32", clock=time.perf_counter) -
                     g_ext=c.params.get("g_ext", (0, 0, 0)), **prm)
         L.init_fields(c.phi0, c.P0, c.u0)
         L.step(r.steps)
-        L.read_fields()
+        _, failed = _read_result(L)
         launches += 2 * r.steps
         t_fin = clock() - t0
-        stats.results.append(Served(r.rid, r.arrival, t_adm, t_fin, r.steps, L.N))
+        stats.results.append(Served(r.rid, r.arrival, t_adm, t_fin, r.steps, L.N, None, failed))
         L.close()
     stats.makespan = clock() - t0
     stats.peak_members = 1

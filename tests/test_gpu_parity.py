@@ -155,25 +155,55 @@ def test_full_trace_filter_f64(lbm):
 # ---------------------------------------------------------------------------
 # FP32 arithmetic against the FP64 oracle
 
-def test_channel_2d_f32_1000_steps(lbm):
-    """128 x 256 layered channel in FP32 against the FP64 oracle.
+def fp32_storage_floor(case, steps):
+    """The FP64 oracle with FP32 storage: after every step the populations,
+    P and u are rounded to FP32 (the rest population of g without its
+    P / (rho_ref T) part, as the FP32 path stores it).  Its difference from
+    the plain oracle is the error FP32 storage alone causes, with exact
+    arithmetic: no FP32 path can be closer to FP64 than this, up to chance."""
+    o = oracle.Oracle(case.lattice, case.shape, oracle.make_params(**case.params), periodic=case.periodic,
+                      solid=case.solid)
+    o.init(case.phi0, case.P0, case.u0)
+    cP = 3.0 / case.params["rho_a"]
 
-    Per step the velocity changes by about the body force g = 1e-7 while the
-    FP32 spacing at max|u| = 0.095 is 7.5e-9, so each step rounds the
-    increment, and in a steady flow it rounds it the same way every step:
-    the drift is bounded by steps x half a spacing = 3.7e-6 = 3.9e-5 max|u|
-    (measured 1.16e-5 max|u| at 1000 steps, rms 6.4e-6).  Pressure errors are
-    acoustic images of velocity errors: |dP| <= rho_w sqrt(T) |du|."""
+    def f32(a):
+        return a.astype(np.float32).astype(np.float64)
+
+    for _ in range(steps):
+        o.step(1)
+        h, g, P, u = o.get_state()
+        Pr = f32(P)
+        g0 = f32(g[0] - P * cP) + Pr * cP
+        g = f32(g)
+        g[0] = g0
+        o.set_state(f32(h), g, Pr, f32(u))
+    return o.fields()
+
+
+def test_channel_2d_f32_1000_steps(lbm):
+    """128 x 256 layered channel in FP32 against the FP64 oracle, 1000 steps.
+
+    Velocity: max|du| <= 1e-5 max|u|.  The body force g = 1e-7 per step
+    against u/T ~ 0.3 is a few FP32 spacings, so the D2Q9 collision forms
+    the odd part of g_eq with one rounding (a float pair); with three
+    roundings the steady flow drifted by 1.2e-5 to 2.5e-5 max|u| in 1000
+    steps.  FP32 storage alone, with exact arithmetic, leaves 7.5e-7.
+    Pressure: this channel's P is only its tiny hydrostatic and capillary
+    part (max|P| = 1.4e-5), below the FP32 resolution of the pressure
+    equation (rho T times a spacing of u, 2.5e-9 a step): FP32 storage alone
+    already leaves 2.1e-4 max|P|, so 1e-6 max|P| is out of reach of any FP32
+    store.  The FP32 path is held to within 6 times that storage floor."""
     c = W.poiseuille_2d(128, 256)
     n = 1000
     _, g = run_gpu(lbm, c, n, storage="f32")
     _, o = run_oracle(c, n)
+    fl = fp32_storage_floor(c, n)
     f1, P1, u1 = g
     f2, P2, u2 = o
-    umax = np.abs(u2).max()
-    du_bound = n * 0.5 * np.spacing(np.float32(umax))
-    assert np.abs(u1 - u2).max() <= du_bound
-    assert np.abs(P1 - P2).max() <= 1.0 * np.sqrt(1.0 / 3.0) * du_bound
+    assert rel(u1[:2], u2[:2]) <= 1e-5, f"u {rel(u1[:2], u2[:2]):.3e}"
+    floor_P = rel(fl[1], P2)
+    assert floor_P > 1e-6                       # the bar is below what FP32 storage allows here
+    assert rel(P1, P2) <= 6 * floor_P, f"P {rel(P1, P2):.3e} vs storage floor {floor_P:.3e}"
     assert np.abs(f1 - f2).max() <= n * 9 * 2 ** -24
 
 
@@ -181,15 +211,22 @@ def test_channel_2d_f32_1000_steps(lbm):
 def test_short_horizon_f32(lbm, lat):
     """Pointwise FP32 vs FP64 over 5 steps (before the interior amplification
     of rounding differences sets in, about step 10 in FP32): velocity to
-    1e-5 max|u|, pressure to 5e-5 of the Laplace scale sigma / R."""
+    1e-5 max|u| and phi to 1e-5.  Pressure to 1e-6 max|P| where FP32
+    storage allows it (the 3D droplet over a film: storage alone leaves
+    about 1e-7); on the 2D droplet, whose P is the Laplace jump
+    (4.6e-5), FP32 storage with exact arithmetic already leaves 4e-6 max|P|,
+    and the FP32 path is held to within 6 times that floor."""
     c = W.droplet_2d(48, 12.0, ux=0.01) if lat == "D2Q9" else small_3d(lat)
-    R = 12.0 if lat == "D2Q9" else 4.0
     _, g = run_gpu(lbm, c, 5, storage="f32")
     _, o = run_oracle(c, 5)
     (f1, P1, u1), (f2, P2, u2) = g, o
     assert np.abs(u1 - u2).max() <= 1e-5 * np.abs(u2).max()
-    assert np.abs(P1 - P2).max() <= 5e-5 * c.params["sigma"] / R
     assert np.abs(f1 - f2).max() <= 1e-5
+    floor_P = rel(fp32_storage_floor(c, 5)[1], P2)
+    if floor_P <= 1e-6 / 4:
+        assert rel(P1, P2) <= 1e-6, f"P {rel(P1, P2):.3e}"
+    else:
+        assert rel(P1, P2) <= 6 * floor_P, f"P {rel(P1, P2):.3e} vs storage floor {floor_P:.3e}"
 
 
 def _wide_3d(geom):
@@ -218,7 +255,7 @@ def test_separable_sums_f32_short_horizon(lbm, geom, variant):
     _, o = run_oracle(c, 5)
     (f1, P1, u1), (f2, P2, u2) = g, o
     assert np.abs(u1 - u2).max() <= 1e-5 * np.abs(u2).max()
-    assert np.abs(P1 - P2).max() <= 5e-5 * c.params["sigma"] / 4.0
+    assert np.abs(P1 - P2).max() <= 1e-6 * np.abs(P2).max()
     assert np.abs(f1 - f2).max() <= 1e-5
 
 
@@ -467,15 +504,24 @@ def test_f32_phase_mass_d3q27(lbm, impact_64_oracle):
     assert abs(L.reduce()["mass"] / phi_o.sum() - 1) <= 1e-6
 
 
-@pytest.mark.parametrize("storage,phi_rms,u_rms", [("f16", 1e-3, 3e-3), ("bf16", 5e-3, 2e-2)])
-def test_reduced_storage_2000_steps(lbm, impact_64_oracle, storage, phi_rms, u_rms):
-    """16-bit storage over 2000 steps of the 64^3 impact (measured: phase
-    mass within 8.7e-5 / 8.2e-5, rms |dphi| 9.8e-5 / 9.6e-4, rms |du| 4.3e-4 /
-    3.4e-3 of max|u| for FP16 / BF16).  The stored sum of a site's h carries
-    one rounding (the moving populations' rounding is taken up by the rest
-    population) and that one is unbiased, so the phase mass does not drift."""
+@pytest.mark.parametrize("storage,phi_rms,u_rms,phi_max,u_max,P_max",
+                         [("f16", 1e-3, 3e-3, 3e-3, 1e-2, 1e-2), ("bf16", 5e-3, 2e-2, 3e-2, 1e-1, 1e-1)])
+def test_reduced_storage_2000_steps(lbm, impact_64_oracle, storage, phi_rms, u_rms, phi_max, u_max, P_max):
+    """16-bit storage over 2000 steps of the 64^3 impact.  Measured for FP16
+    / BF16: phase mass within 9.6e-5 / 9.7e-5; rms |dphi| 1.1e-4 / 9.6e-4,
+    max 1.1e-3 / 1.6e-2; rms |du| 4.4e-4 / 3.5e-3 of max|u|, max 5.4e-3 /
+    5.2e-2; max |dP| 3.1e-3 / 5.3e-2 of max|P|.  So the benchmark spec's
+    "velocity within 1e-3 relative" holds for FP16 in rms but not pointwise
+    over this horizon, and for BF16 in neither (see the Laplace-jump and
+    short-horizon tests for the bars each meets).  The stored sum of a
+    site's h carries one rounding (the moving populations' rounding is taken
+    up by the rest population) and that one is unbiased, so the phase mass
+    does not drift."""
     c, (phi_o, P_o, u_o) = impact_64_oracle
     _, (phi, P, u) = run_gpu(lbm, c, 2000, storage=storage)
     assert abs(phi.sum() / phi_o.sum() - 1) <= 5e-4
     assert np.sqrt(((phi - phi_o) ** 2).mean()) <= phi_rms
     assert np.sqrt(((u - u_o) ** 2).mean()) <= u_rms * np.abs(u_o).max()
+    assert np.abs(phi - phi_o).max() <= phi_max
+    assert np.abs(u - u_o).max() <= u_max * np.abs(u_o).max()
+    assert np.abs(P - P_o).max() <= P_max * np.abs(P_o).max()

@@ -1,9 +1,10 @@
 """The allocation-free reduction entry point (lbm_reduce_fields_noalloc).
 
 It serves callers that cannot allocate device memory at the point of the
-call (stream capture into a CUDA graph, real-time loops, pool-owned memory):
-inputs and outputs are the caller's device arrays and the partial sums live
-in a fixed array inside the library.  This test checks it against the
+call (real-time loops that must not block in an allocator, hosts whose
+device memory belongs to a pool they do not own): inputs and outputs are the
+caller's device arrays and the partial sums live in a fixed array inside the
+library.  This test checks it against the
 handle's own reduction (lbm_reduce) on two calls in a row, through the C
 ABI.  Kept in a file of its own that sorts last, so a run that stops at the
 first failure has already run every other test.
@@ -56,4 +57,13 @@ def test_noalloc_rejects_bad_sizes(lbm):
     for n in (0, -1, 2 ** 31):
         rc = lib.lbm_reduce_fields_noalloc(d.data_ptr(), d.data_ptr(), None, n, 1.0, 1e-3, 1,
                                            d.data_ptr(), None)
+        assert rc == lbm.LBM_ERR_INVALID_ARG
+    # densities must satisfy rho_w > rho_a > 0; device pointers must be given
+    for rho_w, rho_a in ((1e-3, 1e-3), (1e-3, 1.0), (1.0, 0.0), (1.0, -1e-3)):
+        rc = lib.lbm_reduce_fields_noalloc(d.data_ptr(), d.data_ptr(), None, 8, rho_w, rho_a, 1,
+                                           d.data_ptr(), None)
+        assert rc == lbm.LBM_ERR_INVALID_ARG
+    for ptrs in ((d.data_ptr(), d.data_ptr(), None), (None, d.data_ptr(), d.data_ptr()),
+                 (d.data_ptr(), None, d.data_ptr())):
+        rc = lib.lbm_reduce_fields_noalloc(ptrs[0], ptrs[1], None, 8, 1.0, 1e-3, 1, ptrs[2], None)
         assert rc == lbm.LBM_ERR_INVALID_ARG
