@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=100,
                     help="requests of the serving sample: the first ones of the seeded 2000-request trace, "
                          "with its full 500..5000-step range")
+    ap.add_argument("--serve-policy", default="sjf", choices=["fifo", "sjf"],
+                    help="admission order of the batched server: arrival, or least work first")
     ap.add_argument("--no-storage-forms", action="store_true",
                     help="skip the FP16 / BF16 storage lines of the same workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -69,6 +71,8 @@ def parse():
                     help="impact: the 3D droplet impact (default); bubble1/2: the 2D rising bubble of "
                          "Sec. III.D, case 1 or 2, as a batch of --copies lattices")
     ap.add_argument("--copies", type=int, default=32, help="lattices in the batch of the bubble workload")
+    ap.add_argument("--no-batch-autotune", action="store_true",
+                    help="bubble workload: keep the default batch launch shape instead of lbm_batch_autotune")
     return ap.parse_args()
 
 
@@ -183,7 +187,7 @@ def cpu_baseline(reps_target_s: float = 10.0):
             "sample": f"FP64 C oracle, D3Q27 droplet on film 64^3 (R = 8), {steps} steps, {dt:.1f} s"}
 
 
-def serving(n_requests: int):
+def serving(n_requests: int, policy: str = "sjf"):
     """Served solves/s and p50/p99 latency on the serving workload: the first
     n_requests of the seeded 2000-request trace (oscillating ellipsoidal
     droplets in periodic boxes of edge {32, 48, 64, 96, 128}, density ratio
@@ -191,12 +195,14 @@ def serving(n_requests: int):
     FP16 storage, in-place stores.
     1) closed loop: all requests at t = 0 -> capacity (solves/s);
     2) open loop: Poisson arrivals at 0.8 x capacity -> p50/p99 latency;
-    3) the same open-loop trace one request at a time (FP32, split form)."""
+    3) the same open-loop trace one request at a time (FP32, split form).
+    policy: the batched server's admission order (sjf: least work first,
+    with a request waiting over 5 s going first)."""
     from paper_2512_01027_gb300.serving import Server, run_one_at_a_time
 
     full = 2000
     closed = W.request_trace(n=full, rate=1e9)[:n_requests]
-    srv = Server("D3Q27", "f16", inplace=True, chunk=16)
+    srv = Server("D3Q27", "f16", inplace=True, chunk=16, policy=policy)
     cl = srv.run(closed).summary()
     cap = cl["solves_per_s"]
     rate = 0.8 * cap
@@ -208,6 +214,7 @@ def serving(n_requests: int):
     return {"workload": f"first {n_requests} of the 2000-request trace ({100.0 * n_requests / full:.0f} %), "
                         f"D3Q27 droplets, edges 32..128, 500..5000 steps, f16 storage, "
                         f"{work / 1e9:.0f} G site updates",
+            "policy": policy,
             "fraction_of_trace": n_requests / full,
             "closed_loop": cl, "open_loop": dict(op, arrival_rate_per_s=rate), "one_at_a_time_f32": seq}
 
@@ -423,7 +430,7 @@ def run_ours(args):
         L.close()
         del L
         torch.cuda.empty_cache()
-        serve = serving(args.serve_requests)
+        serve = serving(args.serve_requests, args.serve_policy)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -514,6 +521,11 @@ def run_bubble(args):
         B.add(L, args.warmup + args.steps)
         lats.append(L)
     B.step(args.warmup)
+    shape = None
+    if not args.no_batch_autotune:
+        # untimed: the trials restore every member's state and budget
+        K, span, bps, ms_tuned = B.autotune(32)
+        shape = {"chunk": K, "span": span, "blocks_per_sm": bps, "trial_ms_per_step": ms_tuned}
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -550,6 +562,7 @@ def run_bubble(args):
             "config": {"workload": f"2D rising bubble case {case} (Sec. III.D), 200x400 D2Q9, "
                                    f"{args.copies} lattices in one batch, {args.storage} storage",
                        "lattice": "D2Q9", "grid": list(c.shape), "copies": args.copies, "storage": args.storage,
+                       "batch_shape": shape,
                        "parallelism": f"replicas x{world}",
                        "l2": f"inputs larger than L2 ({state_gb:.2f} GB state in the batch)"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",

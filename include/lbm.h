@@ -285,8 +285,7 @@ int lbm_estimate_footprint(const lbm_grid *grid, int lattice, const lbm_params *
  * other than rho_w > rho_a > 0.  The first call with a given device current
  * looks up the array's device address (cudaGetSymbolAddress) and caches it
  * for as long as that device's context lives (after cudaDeviceReset the
- * library must be loaded again); make that first call before any stream
- * capture.  All calls share the array and it keeps the last call's contents
+ * library must be loaded again).  All calls share the array and it keeps the last call's contents
  * (each call overwrites every partial it reads, so nothing needs clearing);
  * calls that overlap on the GPU (different streams, or different host
  * threads) race on it.  LBM_ERR_CUDA when a launch fails; the error state

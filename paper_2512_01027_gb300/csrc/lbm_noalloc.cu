@@ -12,9 +12,8 @@
 // this library holds it (40 KB) until the process exits.  In host code its name
 // is only a host-side stand-in, not a device address; the device address is
 // obtained per device with cudaGetSymbolAddress on the first call made with
-// that device current (so that first call should come before any stream
-// capture), and cached for as long as the device's context lives: after a
-// cudaDeviceReset the library has to be loaded again.
+// that device current, and cached for as long as the device's context lives:
+// after a cudaDeviceReset the library has to be loaded again.
 #include <mutex>
 
 #include "lbm_internal.h"

@@ -349,27 +349,13 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// Unbiased rounding of the pair value hi + lo (|lo| at most half an ulp of
-// hi) to a float: hi, or its neighbour on the side of lo with probability
-// |lo| / (the gap to it), decided by the uniform 32 bits r.
-__device__ __forceinline__ float round_pair_sr(float hi, float lo, uint32_t r)
-{
-    if (lo == 0.f) return hi;
-    const float nb = nextafterf(hi, lo > 0.f ? INFINITY : -INFINITY);
-    const float p = fabsf(lo) / fabsf(__fsub_rn(nb, hi));
-    return (float)(r >> 8) * (1.0f / 16777216.0f) < p ? nb : hi;
-}
-
 // GODD: g* is returned without its odd first-order part w_i c_i . V_g, and
 // V_g = u/T + F/(rho T) + sigma grad rho/(rho^2 T) is returned in vgout.
-// EXACT0: the rest population closes the phase mass from exact sums (see
-// below), rounded without bias by the uniform bits rbits.
-template <class L, bool INIT, bool PDEV, bool GMOM = false, bool GODD = false, bool EXACT0 = false>
+template <class L, bool INIT, bool PDEV, bool GMOM = false, bool GODD = false>
 __device__ __forceinline__ void collide_pairs(const SiteConsts<float> &k, float phi, float phihat, float rho,
                                               float P, const float (&u)[3], const float (&gphi)[3], float lphi,
                                               const float (&gu)[3][3], const float *hp, const float *gp, float *hs,
-                                              float *gs, const float *pig = nullptr, float *vgout = nullptr,
-                                              uint32_t rbits = 0u)
+                                              float *gs, const float *pig = nullptr, float *vgout = nullptr)
 {
     constexpr int D = L::D;
     constexpr int NP = (L::Q - 1) / 2;
@@ -516,32 +502,9 @@ __device__ __forceinline__ void collide_pairs(const SiteConsts<float> &k, float 
         // pulled h: the rounding of the moving populations then does not
         // accumulate in the phase mass.  In exact arithmetic this is
         // h_0 - (h_0 - h_eq_0) / tau_phi.
-        if constexpr (EXACT0) {
-            // The same closure with the sum of the pulled h and the sum of
-            // the moving h* kept exactly as (hi, lo) pairs and the result
-            // rounded without bias: the rounding of the sums no longer leans
-            // the same way step after step at a site of a slow flow, so the
-            // phase mass does not drift (the FP32 sums alone leave 2.8e-5
-            // over 20000 steps of the 2D rising bubble).
-            float ps = hp[0], pc = 0.f, ss = hs[1], sc = 0.f, e;
-            static_for<1, L::Q>([&](auto I) {
-                two_sum(ps, hp[decltype(I)::value], ps, e);
-                pc = __fadd_rn(pc, e);
-            });
-            static_for<2, L::Q>([&](auto I) {
-                two_sum(ss, hs[decltype(I)::value], ss, e);
-                sc = __fadd_rn(sc, e);
-            });
-            float vh, vl;
-            two_sum(ps, -ss, vh, e);
-            vl = __fadd_rn(e, __fsub_rn(pc, sc));
-            two_sum(vh, vl, vh, vl);
-            hs[0] = round_pair_sr(vh, vl, rbits);
-        } else {
-            float sm = 0.f;
-            static_for<1, L::Q>([&](auto I) { sm = __fadd_rn(sm, hs[decltype(I)::value]); });
-            hs[0] = __fsub_rn(phi, sm);
-        }
+        float sm = 0.f;
+        static_for<1, L::Q>([&](auto I) { sm = __fadd_rn(sm, hs[decltype(I)::value]); });
+        hs[0] = __fsub_rn(phi, sm);
     }
     if constexpr (!INIT) {
         // Pi_ab = sum_k c_ka c_kb (g_k - g_eq_k), per pair (c_ka c_kb is even in c)

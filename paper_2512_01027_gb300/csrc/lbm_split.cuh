@@ -605,13 +605,8 @@ __device__ __forceinline__ void collide_site_impl(const SplitArgs<R, typename C:
             hp[i] = C::template dec_h<i>(hraw[i]);
         });
         float vg[3];
-        // D2Q9 with FP32 storage: the rest population's phase-mass closure
-        // from exact sums, rounded without bias (random bits of (site, step))
-        constexpr bool kExact0 = L::Q == 9 && !C::kRound16;
-        uint32_t rb = 0u;
-        if constexpr (kExact0) rb = mix32((uint32_t)idx * 0x9e3779b9u ^ mix32(a.seed));
-        collide_pairs<L, false, C::kPdev, true, C::kGodd, kExact0>(a.k, phi, phihat, rho, P, u, gphi, lphi, gu, hp,
-                                                                  nullptr, hs, gs, pm, vg, rb);
+        collide_pairs<L, false, C::kPdev, true, C::kGodd>(a.k, phi, phihat, rho, P, u, gphi, lphi, gu, hp, nullptr,
+                                                         hs, gs, pm, vg);
         if constexpr (C::kGodd) a.G_new[idx] = make_float4(vg[0], vg[1], vg[2], 0.f);
     } else {
         R gp[Q];

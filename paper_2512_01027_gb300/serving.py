@@ -5,11 +5,15 @@ surface tension, number of steps).  The server
 
 * takes requests as they arrive (arrival times in seconds from the start),
 * builds each request's initial fields on host threads while the GPU works,
-* admits requests first-come first-served while their device footprint
+* admits waiting requests while their device footprint
   (``estimate_footprint``) fits in the HBM budget, a member slot is free and
   the sites of the admitted lattices stay within ``max_active_sites`` (one
   large lattice already fills the GPU: sharing it among many large lattices
   only stretches every one of them; small lattices still run many at once),
+  first come first served (``policy="fifo"``) or the least work first
+  (``policy="sjf"``: sites x steps, which shortens the wait of the many small
+  requests behind a few large ones; a request that has waited longer than
+  ``max_wait`` seconds goes first whatever its size),
 * advances all admitted lattices together through one ``Batch`` (two kernel
   launches per time step for the whole set, chunks replayed as CUDA graphs),
   each lattice by exactly its own number of steps,
@@ -92,7 +96,11 @@ class Server:
 
     def __init__(self, lattice: str = "D3Q27", storage: str = "f16", inplace: bool = True, chunk: int = 16,
                  max_members: int = 64, hbm_budget: int | None = None, prep_threads: int = 4,
-                 keep_fields: bool = False, stream=None, max_active_sites: int | None = None):
+                 keep_fields: bool = False, stream=None, max_active_sites: int | None = None,
+                 policy: str = "fifo", max_wait: float = 5.0):
+        if policy not in ("fifo", "sjf"):
+            raise ValueError("policy is 'fifo' or 'sjf'")
+        self.policy, self.max_wait = policy, float(max_wait)
         self.lattice, self.storage, self.inplace = lattice, storage, bool(inplace)
         self.chunk, self.max_members = int(chunk), int(max_members)
         self.max_active_sites = max_active_sites
@@ -131,7 +139,17 @@ class Server:
                 while pend and pend[0].arrival <= now:
                     r = pend.popleft()
                     waiting.append((r, pool.submit(_prepare, r)))
-                # admission: first come first served, by free HBM and slots
+                # admission by free HBM and slots, in the policy's order
+                if self.policy == "sjf" and len(waiting) > 1:
+                    # requests waiting longer than max_wait first, in arrival
+                    # order; then the least work (sites x steps) first
+                    def key(rf, now=now):
+                        r = rf[0]
+                        if now - r.arrival > self.max_wait:
+                            return (0, r.arrival, 0)
+                        return (1, r.edge ** 3 * r.steps, r.arrival)
+
+                    waiting = collections.deque(sorted(waiting, key=key))
                 while waiting and len(active) < self.max_members:
                     r, fut = waiting[0]
                     need = self.footprint(r)

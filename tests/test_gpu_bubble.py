@@ -86,15 +86,18 @@ def test_bubble_rises_at_most_at_the_added_mass_rate(lbm, case):
 
 @pytest.mark.parametrize("case", [1, 2])
 def test_bubble_f32_phase_mass(lbm, case):
-    """FP32 storage keeps the phase mass of the rising bubble to 1e-6 over
-    20000 steps.  The collision stores as the rest population what the
-    moving ones leave of the pulled phi; with the two sums kept exactly (as
-    pairs of floats) and that population rounded without bias, the per-step
-    errors of a site no longer lean one way in the slow flow (with plain
-    FP32 sums the mass grew by 2.8e-5 over these steps)."""
+    """FP32 storage and the phase mass of the rising bubble over 20000 steps.
+    The collision stores as the rest population what the moving ones leave
+    of the pulled phi, which takes the weights' rounding and the moving
+    populations' rounding out of the mass; what remains (2.8e-5 here) is the
+    rounding of the two FP32 sums, which in a slow flow leans the same way
+    at a site step after step.  Summing exactly and rounding that population
+    without bias removed it (below 1e-6), but the random flips it puts into
+    phi destabilised the sheared layered channel within 9000-16000 steps, so
+    it is not built; the bound here guards the closure (without it: 1.6e-4)."""
     c = W.rising_bubble_2d(case)
     L, _ = run_gpu(lbm, c, 0, storage="f32")
     m0 = L.reduce()["mass"]
     L.step(20000)
     L.check()
-    assert abs(L.reduce()["mass"] / m0 - 1) <= 1e-6
+    assert abs(L.reduce()["mass"] / m0 - 1) <= 1e-4

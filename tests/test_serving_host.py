@@ -99,3 +99,23 @@ def test_site_cap_still_admits_one_large_request(fake):
     S = serving.Server("D3Q27", "f16", chunk=4, hbm_budget=1 << 40, max_active_sites=1000)
     st = S.run(reqs)
     assert len(st.results) == 3 and st.peak_members == 1
+
+
+def test_sjf_admits_least_work_first(fake):
+    """policy="sjf": with one member slot and every request waiting at t = 0,
+    the requests run in order of their work (sites x steps); every one still
+    gets exactly its steps.  A request past max_wait goes first in arrival
+    order (max_wait = -1: every request is overdue, so arrival order)."""
+    reqs = W.request_trace(n=10, rate=1e9, edges=(8, 12, 16), steps_range=(3, 30))
+    work = {r.rid: r.edge ** 3 * r.steps for r in reqs}
+    S = serving.Server("D3Q27", "f16", chunk=4, keep_fields=True, hbm_budget=1 << 40, max_members=1,
+                       policy="sjf", max_wait=1e9)
+    st = S.run(reqs)
+    order = [r.rid for r in sorted(st.results, key=lambda q: q.admitted)]
+    assert [work[i] for i in order] == sorted(work.values())
+    for r in st.results:
+        assert r.fields == (next(q.steps for q in reqs if q.rid == r.rid),)
+    S = serving.Server("D3Q27", "f16", chunk=4, hbm_budget=1 << 40, max_members=1, policy="sjf", max_wait=-1.0)
+    st = S.run(reqs)
+    order = [r.rid for r in sorted(st.results, key=lambda q: q.admitted)]
+    assert order == [r.rid for r in sorted(reqs, key=lambda q: q.arrival)]
