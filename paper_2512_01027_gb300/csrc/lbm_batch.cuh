@@ -52,23 +52,40 @@ __device__ __forceinline__ void batch_site(const SplitArgs<R, typename C::S> &a,
     else collide_site<L, R, C, HAS_MASK, MODE, uint32_t>(a, idx);
 }
 
-// PHASE 0: S0 + S1 of every member; PHASE 1: S0 + S2..S5.
+// FP32 D2Q9 (4-byte storage, no stochastic rounding of a rest population):
+// the site code reads the member's arguments from the table (read-only,
+// cached) instead of a copy held in registers through the item, which lets
+// the kernels run at 96 registers without spills, 5 blocks per SM (6 for the
+// moments) instead of 4.  The others copy the arguments into registers per
+// item and run 4 blocks per SM with FP32 arithmetic (128 registers; the
+// collision spills a little, which costs less than a fourth of the warps: a
+// batch of eight 128^3 D3Q27 lattices ran 2-5 % faster than at 3 blocks and
+// 168 registers), 3 with FP64 (at 4 its site code spills kilobytes).
+// Read by reference, or staged in shared memory, their site code needed
+// more registers or ran slower.
+template <class L, class R, class C>
+inline constexpr bool kBatchArgsByRef = kPacked<R> && L::Q == 9 && !C::kRound16;
+
 template <class L, class R, class C, int PHASE>
-__global__ void __launch_bounds__(kSplitThreads, 3)
-    batch_kernel(const BatchHeader *__restrict__ hdr, const BatchMember<R, typename C::S> *__restrict__ mem, int k)
+constexpr int batch_min_blocks()
 {
-    using S = typename C::S;
-    const int nmem = (int)hdr->nmem;
-    const long long total = hdr->active[k];
-    const int span = (int)hdr->span;
-    for (long long t = blockIdx.x; t < total; t += gridDim.x) {
-        const int j = batch_find(mem, nmem, t);
-        const int q = k & 1;
-        SplitArgs<R, S> a = mem[j].a[q];
-        a.seed += (unsigned)(k - q);   // a[q] holds the chunk's first steps; step k of the chunk
-        const int mode = mem[j].mode[q];
-        const bool masked = mem[j].has_mask != 0;
-        const long long base = (t - mem[j].first_item) * span * kSplitThreads + threadIdx.x;
+    return kBatchArgsByRef<L, R, C> ? (PHASE == 1 ? 5 : 6) : (kPacked<R> ? 4 : 3);
+}
+
+// The item t of member j (base: its first site for this thread) in PHASE.
+template <class L, class R, class C, int PHASE>
+__device__ __forceinline__ void batch_item(const SplitArgs<R, typename C::S> &a, int mode, bool masked,
+                                           long long base, int span)
+{
+    if constexpr (PHASE == 2) {
+        if (!a.k.coupling) return;
+        for (int s = 0; s < span; ++s) {
+            const long long lidx = base + (long long)s * kSplitThreads;
+            if (lidx >= a.N) break;
+            if (masked) coupling_site<L, R, C, true, uint32_t>(a, (int)lidx);
+            else coupling_site<L, R, C, false, uint32_t>(a, (int)lidx);
+        }
+    } else {
         for (int s = 0; s < span; ++s) {
             const long long lidx = base + (long long)s * kSplitThreads;
             if (lidx >= a.N) break;   // past the member's last site (so are the item's later blocks)
@@ -82,6 +99,33 @@ __global__ void __launch_bounds__(kSplitThreads, 3)
                 else if (mode == kAAOdd) batch_site<L, R, C, PHASE, false, kAAOdd>(a, idx);
                 else batch_site<L, R, C, PHASE, false, kAAEven>(a, idx);
             }
+        }
+    }
+}
+
+// PHASE 0: S0 + S1 of every member; PHASE 1: S0 + S2..S5; PHASE 2 (between
+// the two, when some member takes it): the u^{n+1} coupling's omega-term of
+// P^{n+1} for those members.
+template <class L, class R, class C, int PHASE>
+__global__ void __launch_bounds__(kSplitThreads, batch_min_blocks<L, R, C, PHASE>())
+    batch_kernel(const BatchHeader *__restrict__ hdr, const BatchMember<R, typename C::S> *__restrict__ mem, int k)
+{
+    using S = typename C::S;
+    const int nmem = (int)hdr->nmem;
+    const long long total = hdr->active[k];
+    const int span = (int)hdr->span;
+    for (long long t = blockIdx.x; t < total; t += gridDim.x) {
+        const int j = batch_find(mem, nmem, t);
+        const int q = k & 1;
+        const int mode = mem[j].mode[q];
+        const bool masked = mem[j].has_mask != 0;
+        const long long base = (t - mem[j].first_item) * span * kSplitThreads + threadIdx.x;
+        if constexpr (kBatchArgsByRef<L, R, C>) {
+            batch_item<L, R, C, PHASE>(mem[j].a[q], mode, masked, base, span);
+        } else {
+            SplitArgs<R, S> a = mem[j].a[q];
+            a.seed += (unsigned)(k - q);   // a[q] holds the chunk's first steps; step k of the chunk
+            batch_item<L, R, C, PHASE>(a, mode, masked, base, span);
         }
     }
 }

@@ -89,11 +89,14 @@ struct Impl {
     static void launch_split_ix(lbm_ctx *c, const SplitArgs<R, S> &a)
     {
         const unsigned blocks = (unsigned)((c->N + kSplitThreads - 1) / kSplitThreads);
+        // with the u^{n+1} coupling, the omega-term of P^{n+1} between the two
         if (c->has_mask) {
             moments_kernel<L, R, C, true, MODE, IX><<<blocks, kSplitThreads, 0, c->stream>>>(a);
+            if (c->consts.coupling) coupling_kernel<L, R, C, true, IX><<<blocks, kSplitThreads, 0, c->stream>>>(a);
             collide_kernel<L, R, C, true, MODE, IX><<<blocks, kSplitThreads, 0, c->stream>>>(a);
         } else {
             moments_kernel<L, R, C, false, MODE, IX><<<blocks, kSplitThreads, 0, c->stream>>>(a);
+            if (c->consts.coupling) coupling_kernel<L, R, C, false, IX><<<blocks, kSplitThreads, 0, c->stream>>>(a);
             collide_kernel<L, R, C, false, MODE, IX><<<blocks, kSplitThreads, 0, c->stream>>>(a);
         }
     }
@@ -114,6 +117,9 @@ struct Impl {
         a.err = c->d_err;
         a.nx = c->nx; a.ny = c->ny; a.nz = c->nz;
         a.N = c->N;
+        // one thread a site from site 0 (split launches, batch items of whole
+        // 128-site blocks): whole warps when N is a multiple of 32
+        a.vote = (c->N & 31) == 0;
         a.k = site_consts<R>(c->consts);
         a.phi = static_cast<R *>(c->phi);
         const int src = c->cur ^ flip, dst = 1 - src;
@@ -270,13 +276,14 @@ struct Impl {
         return per_sm * (sms > 0 ? sms : 1);
     }
 
-    static cudaError_t batch_launch(cudaStream_t s, const void *d_table, int K, int grid0, int grid1)
+    static cudaError_t batch_launch(cudaStream_t s, const void *d_table, int K, int grid0, int grid1, bool coupled)
     {
         const BatchHeader *hdr = static_cast<const BatchHeader *>(d_table);
         const BatchMember<R, S> *mem = reinterpret_cast<const BatchMember<R, S> *>(
             static_cast<const char *>(d_table) + batch_header_bytes());
         for (int k = 0; k < K; ++k) {
             batch_kernel<L, R, C, 0><<<grid0, kSplitThreads, 0, s>>>(hdr, mem, k);
+            if (coupled) batch_kernel<L, R, C, 2><<<grid1, kSplitThreads, 0, s>>>(hdr, mem, k);
             batch_kernel<L, R, C, 1><<<grid1, kSplitThreads, 0, s>>>(hdr, mem, k);
         }
         return cudaGetLastError();
@@ -314,7 +321,9 @@ struct Impl {
             int rc = cuda_fail(c, cudaMemsetAsync(c->pctl, 0, sizeof(int) * (2 + (size_t)p.nz), c->stream),
                                "cudaMemsetAsync(persistent counters)");
             if (rc != LBM_OK) return rc;
-            split_persistent_kernel<L, C, M, MODE><<<g, kSplitThreads, 0, c->stream>>>(a, p);
+            SplitArgs<R, S> ap = a;
+            ap.vote = (p.nxy & 31) == 0;   // items are blocks of one plane
+            split_persistent_kernel<L, C, M, MODE><<<g, kSplitThreads, 0, c->stream>>>(ap, p);
             return cuda_fail(c, cudaGetLastError(), "split_persistent_kernel launch");
         } else {
             return LBM_ERR_UNSUPPORTED;

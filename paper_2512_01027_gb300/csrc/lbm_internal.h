@@ -109,7 +109,8 @@ struct lbm_batch_ctx {
     size_t cap_members = 0;
     void *d_table = nullptr;
     void *h_table = nullptr;          // pinned staging copy
-    std::vector<std::pair<int, cudaGraphExec_t>> graphs;   // per chunk length
+    std::vector<std::pair<int, cudaGraphExec_t>> graphs;   // per (chunk length, coupled): key 2 K + coupled
+    bool coupled = false;             // the current table has a member with the u^{n+1} coupling
     int grid[2] = {0, 0};
     int span = 1;                     // 128-site blocks per work item
     int blocks_per_sm = 0;            // persistent blocks per SM (0: the kernels' occupancy)
@@ -139,7 +140,8 @@ struct Ops {
     long long (*batch_items)(const lbm_ctx *c, int span);
     void (*batch_fill)(const lbm_ctx *c, int take, long long first_item, void *dst);
     int (*batch_grid)(int phase, int blocks_per_sm);
-    cudaError_t (*batch_launch)(cudaStream_t s, const void *d_table, int K, int grid0, int grid1);
+    // coupled: some member takes the u^{n+1} coupling (a third launch per step)
+    cudaError_t (*batch_launch)(cudaStream_t s, const void *d_table, int K, int grid0, int grid1, bool coupled);
     // cluster step (variant 5) with `rows` CTAs per cluster
     bool (*cluster_ok)(const lbm_ctx *c, int rows);
 };

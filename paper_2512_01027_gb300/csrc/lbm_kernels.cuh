@@ -244,6 +244,8 @@ struct SplitArgs {
     int *err;
     int nx, ny, nz;
     long long N;
+    int vote;                 // 1: the launch hands each warp to the per-site code with all 32 lanes,
+                              // so the site code may take a warp vote
     SiteConsts<R> k;
 };
 

@@ -410,18 +410,26 @@ __device__ __forceinline__ auto split_sink(const SplitArgs<float, typename C::S>
 }
 
 // S0 + S1 at site idx with FP32 arithmetic, results to sink(u_x, u_y, u_z,
-// P^{n+1}, phi^{n+1}, pm).  With nx a multiple of 32 every warp is 32
-// consecutive sites of one row, and a warp whose sites have no solid or
-// outside neighbour takes the separable sums, or at least the code without
-// bounce-back selections.  Every lane of the warp calls it (warp vote).
+// P^{n+1}, phi^{n+1}, pm).  A warp whose sites have no solid or outside
+// neighbour (a warp vote, where a.vote says that all 32 lanes call this
+// together) takes the code without bounce-back selections.  D3Q27 takes the
+// separable sums there instead, which need the warp's 32 sites in one row
+// (nx a multiple of 32); with other nx it keeps one copy of the pair code,
+// so the kernel does not carry three.
 template <class L, class C, bool HAS_MASK, int MODE, class IX, class Pull, class Sink>
 __device__ __forceinline__ void moments_site_f32(const SplitArgs<float, typename C::S> &a, const int idx,
                                                  const uint32_t m, const Pull &pull, Sink &&sink)
 {
-    if ((a.nx & 31) == 0 && !(HAS_MASK && __any_sync(0xffffffffu, m != 0u))) {
-        if constexpr (kSepForm<L, float, C>) moments_site_sep<L, C, MODE, IX>(a, idx, pull, sink);
-        else moments_site_packed<L, C, false, MODE, IX>(a, idx, 0u, pull, sink);
-        return;
+    if constexpr (kSepForm<L, float, C>) {
+        if ((a.nx & 31) == 0 && !(HAS_MASK && __any_sync(0xffffffffu, m != 0u))) {
+            moments_site_sep<L, C, MODE, IX>(a, idx, pull, sink);
+            return;
+        }
+    } else {
+        if (!HAS_MASK || (a.vote && !__any_sync(0xffffffffu, m != 0u))) {
+            moments_site_packed<L, C, false, MODE, IX>(a, idx, 0u, pull, sink);
+            return;
+        }
     }
     if (m & kSolidBit) return;
     moments_site_packed<L, C, HAS_MASK, MODE, IX>(a, idx, m, pull, sink);
@@ -565,38 +573,6 @@ __device__ __forceinline__ void collide_site_impl(const SplitArgs<R, typename C:
     }
     const R phihat = a.k.clamp ? clamp01(phi) : phi;
     const R rho = a.k.rho_a + phihat * a.k.drho;
-    if (a.k.coupling) {
-        // The alternative reading of the pressure formula: the omega-term
-        // omega rho_ref sum_i w_i c_i . u(x - c_i) with the new velocity,
-        // whose neighbours the moments launch did not have yet.
-        const R omega = (rho - a.k.rho_a) / a.k.drho * a.k.om1;
-        R swcu = R(0);
-        if constexpr (kPacked<R>) {
-            // sum_i w_i c_i . u(x - c_i) = -T div u with the pair stencil's
-            // divergence (the same wall rule: u = 0 at a solid neighbour)
-            R div = gu[0][0] + gu[1][1];
-            if constexpr (D == 3) div = div + gu[2][2];
-            swcu = div * R(-1.0 / 3.0);
-        } else {
-            // the canonical order of the moments' own sum
-            static_for<1, Q>([&](auto I) {
-                constexpr int i = decltype(I)::value;
-                if (!(HAS_MASK && ((m >> i) & 1u))) {
-                    const int src = nb.at<L, i>(-1);
-                    R un[3];
-                    static_for<0, 3>([&](auto A) {
-                        constexpr int ax = decltype(A)::value;
-                        if constexpr (ax < D && L::c(i, ax) != 0) un[ax] = a.u_new[eidx<IX>(ax, N, src)];
-                        else un[ax] = R(0);
-                    });
-                    swcu = swcu + R(L::w(i)) * dot_c<L, i>(un);
-                }
-            });
-        }
-        P = P + omega * a.k.rho_a * swcu;
-        if constexpr (kPacked<R>) a.F_new[idx].w = P;
-        else a.P_new[idx] = P;
-    }
     R hp[Q], hs[Q], gs[Q];
     if constexpr (kPacked<R>) {
         if constexpr (!kEarlyH) load_h_pig();
@@ -635,12 +611,11 @@ __device__ __forceinline__ void collide_site_impl(const SplitArgs<R, typename C:
         atomicOr(a.err, 1);
 }
 
-// S0 + S2..S5 at site idx.  With FP32 arithmetic and nx a multiple of 32
-// (whole warps in one row), a warp whose sites have no solid or outside
-// neighbour runs the code without bounce-back selections (the same
-// arithmetic: with no mask bit set both give the same bits).  Not in the
-// even step of the in-place store: there the two copies of the code need
-// more registers than it has.
+// S0 + S2..S5 at site idx.  With FP32 arithmetic and whole warps (a.vote),
+// a warp whose sites have no solid or outside neighbour runs the code
+// without bounce-back selections (the same arithmetic: with no mask bit set
+// both give the same bits).  Not in the even step of the in-place store:
+// there the two copies of the code need more registers than it has.
 template <class L, class R, class C, bool HAS_MASK, int MODE, class IX, bool CG = false>
 __device__ __forceinline__ void collide_site(const SplitArgs<R, typename C::S> &a, const int idx)
 {
@@ -648,13 +623,74 @@ __device__ __forceinline__ void collide_site(const SplitArgs<R, typename C::S> &
     if constexpr (HAS_MASK) {
         m = a.mask[idx];
         if constexpr (kPacked<R> && MODE != kAAEven) {
-            if ((a.nx & 31) == 0 && !__any_sync(0xffffffffu, m != 0u)) {
+            if (a.vote && !__any_sync(0xffffffffu, m != 0u)) {
                 collide_site_impl<L, R, C, false, MODE, IX, CG>(a, idx, 0u);
                 return;
             }
         }
     }
     collide_site_impl<L, R, C, HAS_MASK, MODE, IX, CG>(a, idx, m);
+}
+
+// The u^{n+1} reading of the pressure formula's omega-term (coupling_unew):
+// omega rho_ref sum_i w_i c_i . u(x - c_i) taken with the new velocity,
+// whose neighbours the moments launch does not have yet.  The moments leave
+// the term out of P^{n+1}; this adds it at a fluid site before the
+// collision reads P^{n+1}.  FP32 arithmetic: sum_i w_i c_i . u(x - c_i) =
+// -T div u with the divergence of the collision's pair stencil over the
+// packed (u, phi) words (u = 0 at a solid neighbour); FP64: the sum over the
+// directions in the canonical order of the moments' own sum.
+template <class L, class R, class C, bool HAS_MASK, class IX>
+__device__ __forceinline__ void coupling_site(const SplitArgs<R, typename C::S> &a, const int idx)
+{
+    constexpr int D = L::D, Q = L::Q;
+    uint32_t m = 0;
+    if constexpr (HAS_MASK) m = a.mask[idx];
+    if (m & kSolidBit) return;
+    const IX N = (IX)a.N;
+    const Nbr32 nb(idx, a.nx, a.ny, D == 3 ? a.nz : 1);
+    R phi, swcu = R(0);
+    if constexpr (kPacked<R>) {
+        float gphi[3], lphi, gu[3][3];
+        phi = a.FB[idx].w;
+        auto at = [&](auto I, int s) { return a.FB[nb.at<L, decltype(I)::value>(s)]; };
+        if (m == 0u) stencil_packed<L, false>(at, m, phi, gphi, lphi, gu);
+        else stencil_packed<L, true>(at, m, phi, gphi, lphi, gu);
+        float div = gu[0][0] + gu[1][1];
+        if constexpr (D == 3) div = div + gu[2][2];
+        swcu = div * float(-1.0 / 3.0);
+    } else {
+        phi = a.phi[idx];
+        static_for<1, Q>([&](auto I) {
+            constexpr int i = decltype(I)::value;
+            if (!(HAS_MASK && ((m >> i) & 1u))) {
+                const int src = nb.at<L, i>(-1);
+                R un[3];
+                static_for<0, 3>([&](auto A) {
+                    constexpr int ax = decltype(A)::value;
+                    if constexpr (ax < D && L::c(i, ax) != 0) un[ax] = a.u_new[eidx<IX>(ax, N, src)];
+                    else un[ax] = R(0);
+                });
+                swcu = swcu + R(L::w(i)) * dot_c<L, i>(un);
+            }
+        });
+    }
+    const R phihat = a.k.clamp ? clamp01(phi) : phi;
+    const R rho = a.k.rho_a + phihat * a.k.drho;
+    const R omega = (rho - a.k.rho_a) / a.k.drho * a.k.om1;
+    if constexpr (kPacked<R>) {
+        float4 *w = a.F_new + idx;
+        w->w = w->w + omega * a.k.rho_a * swcu;
+    } else {
+        a.P_new[idx] = a.P_new[idx] + omega * a.k.rho_a * swcu;
+    }
+}
+
+template <class L, class R, class C, bool HAS_MASK, class IX>
+__global__ void __launch_bounds__(kSplitThreads) coupling_kernel(const SplitArgs<R, typename C::S> a)
+{
+    const long long idx = (long long)blockIdx.x * kSplitThreads + threadIdx.x;
+    if (idx < a.N) coupling_site<L, R, C, HAS_MASK, IX>(a, (int)idx);
 }
 
 template <class L, class R, class C, bool HAS_MASK, int MODE, class IX>
