@@ -62,8 +62,11 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=100,
                     help="requests of the serving sample: the first ones of the seeded 2000-request trace, "
                          "with its full 500..5000-step range")
-    ap.add_argument("--serve-policy", default="sjf", choices=["fifo", "sjf"],
-                    help="admission order of the batched server: arrival, or least work first")
+    ap.add_argument("--serve-policy", default="srpt", choices=["fifo", "sjf", "srpt"],
+                    help="batched server: admission in arrival order, or least work first; srpt also steps "
+                         "only the lattices with the least work left in each chunk")
+    ap.add_argument("--serve-fill", type=int, default=1 << 21,
+                    help="srpt: sites stepped per chunk (lattices with the least work left first)")
     ap.add_argument("--no-storage-forms", action="store_true",
                     help="skip the FP16 / BF16 storage lines of the same workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -187,7 +190,7 @@ def cpu_baseline(reps_target_s: float = 10.0):
             "sample": f"FP64 C oracle, D3Q27 droplet on film 64^3 (R = 8), {steps} steps, {dt:.1f} s"}
 
 
-def serving(n_requests: int, policy: str = "sjf"):
+def serving(n_requests: int, policy: str = "srpt", fill_sites: int = 1 << 21):
     """Served solves/s and p50/p99 latency on the serving workload: the first
     n_requests of the seeded 2000-request trace (oscillating ellipsoidal
     droplets in periodic boxes of edge {32, 48, 64, 96, 128}, density ratio
@@ -196,13 +199,15 @@ def serving(n_requests: int, policy: str = "sjf"):
     1) closed loop: all requests at t = 0 -> capacity (solves/s);
     2) open loop: Poisson arrivals at 0.8 x capacity -> p50/p99 latency;
     3) the same open-loop trace one request at a time (FP32, split form).
-    policy: the batched server's admission order (sjf: least work first,
-    with a request waiting over 5 s going first)."""
+    policy: the batched server's order (sjf: admission by least work first,
+    with a request waiting over 5 s going first; srpt: in addition, each
+    chunk steps only the lattices with the least work left, up to fill_sites
+    sites, and pauses the others)."""
     from paper_2512_01027_gb300.serving import Server, run_one_at_a_time
 
     full = 2000
     closed = W.request_trace(n=full, rate=1e9)[:n_requests]
-    srv = Server("D3Q27", "f16", inplace=True, chunk=16, policy=policy)
+    srv = Server("D3Q27", "f16", inplace=True, chunk=16, policy=policy, fill_sites=fill_sites)
     cl = srv.run(closed).summary()
     cap = cl["solves_per_s"]
     rate = 0.8 * cap
@@ -214,7 +219,7 @@ def serving(n_requests: int, policy: str = "sjf"):
     return {"workload": f"first {n_requests} of the 2000-request trace ({100.0 * n_requests / full:.0f} %), "
                         f"D3Q27 droplets, edges 32..128, 500..5000 steps, f16 storage, "
                         f"{work / 1e9:.0f} G site updates",
-            "policy": policy,
+            "policy": policy, "fill_sites": fill_sites if policy == "srpt" else None,
             "fraction_of_trace": n_requests / full,
             "closed_loop": cl, "open_loop": dict(op, arrival_rate_per_s=rate), "one_at_a_time_f32": seq}
 
@@ -430,7 +435,7 @@ def run_ours(args):
         L.close()
         del L
         torch.cuda.empty_cache()
-        serve = serving(args.serve_requests, args.serve_policy)
+        serve = serving(args.serve_requests, args.serve_policy, args.serve_fill)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

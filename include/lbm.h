@@ -383,6 +383,13 @@ int lbm_batch_step(lbm_batch b, int64_t n, int *finished);
 /* Remaining budget of member h. */
 int lbm_batch_remaining(lbm_batch b, lbm_handle h, int64_t *steps_left);
 
+/* Pauses (paused = 1) or resumes (0) member h: a paused member takes no
+ * steps in lbm_batch_step and keeps its budget, its state and its device
+ * memory; the others step as before.  A serving loop uses it to give the
+ * GPU to the members with the least work left.  Members join unpaused.
+ * LBM_ERR_INVALID_ARG if h is not a member or paused is not 0 or 1. */
+int lbm_batch_pause(lbm_batch b, lbm_handle h, int32_t paused);
+
 /* Members and kernel launches issued so far (either may be NULL). */
 int lbm_batch_info(lbm_batch b, int *members, int64_t *launches);
 

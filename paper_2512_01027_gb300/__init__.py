@@ -107,6 +107,7 @@ SIGNATURES = {
     "lbm_batch_remove": (ctypes.c_int, [_vp, _vp]),
     "lbm_batch_step": (ctypes.c_int, [_vp, _i64, ctypes.POINTER(ctypes.c_int)]),
     "lbm_batch_remaining": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_i64)]),
+    "lbm_batch_pause": (ctypes.c_int, [_vp, _vp, ctypes.c_int32]),
     "lbm_batch_info": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_i64)]),
     "lbm_batch_last_error": (ctypes.c_char_p, [_vp]),
 }
@@ -450,9 +451,13 @@ class Batch:
         _bcheck(lib().lbm_batch_remove(self._b, lat.handle), self._b)
         self.members.remove(lat)
 
+    def pause(self, lat: "Lattice", paused: bool = True):
+        """A paused member takes no steps (budget, state and memory kept)."""
+        _bcheck(lib().lbm_batch_pause(self._b, lat.handle, int(bool(paused))), self._b)
+
     def step(self, n: int) -> int:
-        """Advance every member by min(n, its remaining budget); returns the
-        number of members whose budget is spent."""
+        """Advance every unpaused member by min(n, its remaining budget);
+        returns the number of members whose budget is spent."""
         f = ctypes.c_int()
         _bcheck(lib().lbm_batch_step(self._b, int(n), ctypes.byref(f)), self._b)
         return f.value

@@ -197,6 +197,7 @@ int lbm_batch_add(lbm_batch b, lbm_handle h, int64_t steps)
     cudaStreamSynchronize(h->stream);
     b->members.push_back(h);
     b->remaining.push_back(steps);
+    b->paused.push_back(0);
     h->batch = b;
     return LBM_OK;
 }
@@ -209,6 +210,7 @@ int lbm_batch_remove(lbm_batch b, lbm_handle h)
     cudaStreamSynchronize(b->stream);
     b->members.erase(b->members.begin() + j);
     b->remaining.erase(b->remaining.begin() + j);
+    b->paused.erase(b->paused.begin() + j);
     h->batch = nullptr;
     return LBM_OK;
 }
@@ -225,7 +227,7 @@ int lbm_batch_step(lbm_batch b, int64_t n, int *finished)
         order.clear();
         take.assign(b->members.size(), 0);
         for (size_t j = 0; j < b->members.size(); ++j) {
-            take[j] = (int)std::min<int64_t>(K, b->remaining[j]);
+            take[j] = b->paused[j] ? 0 : (int)std::min<int64_t>(K, b->remaining[j]);
             if (take[j] > 0) order.push_back((int)j);
         }
         if (order.empty()) break;
@@ -295,6 +297,16 @@ int lbm_batch_step(lbm_batch b, int64_t n, int *finished)
     return rc;
 }
 
+int lbm_batch_pause(lbm_batch b, lbm_handle h, int32_t paused)
+{
+    if (!b || !h) return LBM_ERR_INVALID_ARG;
+    if (paused != 0 && paused != 1) return bfail(b, LBM_ERR_INVALID_ARG, "paused is 0 or 1");
+    const int j = find_member(b, h);
+    if (j < 0) return bfail(b, LBM_ERR_INVALID_ARG, "the handle is not a member of this batch");
+    b->paused[j] = (char)paused;
+    return LBM_OK;
+}
+
 int lbm_batch_remaining(lbm_batch b, lbm_handle h, int64_t *steps_left)
 {
     if (!b || !h || !steps_left) return LBM_ERR_INVALID_ARG;
@@ -328,6 +340,8 @@ int lbm_batch_autotune(lbm_batch b, int trial_steps, int *chunk, int *span, int 
     // every member's state and budget, restored after the trials
     std::vector<std::vector<char>> saved(b->members.size());
     std::vector<int64_t> budget = b->remaining;
+    const std::vector<char> paused = b->paused;   // every member steps in the trials
+    std::fill(b->paused.begin(), b->paused.end(), 0);
     int rc = LBM_OK;
     for (size_t j = 0; j < b->members.size() && rc == LBM_OK; ++j) {
         size_t bytes = 0;
@@ -337,7 +351,10 @@ int lbm_batch_autotune(lbm_batch b, int trial_steps, int *chunk, int *span, int 
             rc = lbm_save_state(b->members[j], saved[j].data(), bytes);
         }
     }
-    if (rc != LBM_OK) return bfail(b, rc, "saving a member's state failed");
+    if (rc != LBM_OK) {
+        b->paused = paused;
+        return bfail(b, rc, "saving a member's state failed");
+    }
     const int chunk0 = b->chunk, span0 = b->span, bps0 = b->blocks_per_sm;
     int occ = 0;
     {
@@ -394,6 +411,7 @@ int lbm_batch_autotune(lbm_batch b, int trial_steps, int *chunk, int *span, int 
         if (r != LBM_OK && rc_restore == LBM_OK) rc_restore = r;
     }
     b->remaining = budget;
+    b->paused = paused;
     if (rc != LBM_OK) {
         lbm_batch_set_shape(b, span0, bps0);
         lbm_batch_set_tuning(b, chunk0, b->use_graph ? 1 : 0);

@@ -103,6 +103,7 @@ struct lbm_batch_ctx {
     bool own_stream = false;
     std::vector<lbm_ctx *> members;
     std::vector<int64_t> remaining;   // steps each member still has to take
+    std::vector<char> paused;         // members that take no steps for now
     int chunk = 16;                   // steps per chunk (one graph launch)
     bool use_graph = true;
     size_t table_bytes = 0;           // header + capacity members

@@ -11,12 +11,21 @@ surface tension, number of steps).  The server
   large lattice already fills the GPU: sharing it among many large lattices
   only stretches every one of them; small lattices still run many at once),
   first come first served (``policy="fifo"``) or the least work first
-  (``policy="sjf"``: sites x steps, which shortens the wait of the many small
-  requests behind a few large ones; a request that has waited longer than
-  ``max_wait`` seconds goes first whatever its size),
-* advances all admitted lattices together through one ``Batch`` (two kernel
+  (``policy="sjf"`` and ``"srpt"``: sites x steps, which shortens the wait of
+  the many small requests behind a few large ones; a request that has
+  waited longer than ``max_wait`` seconds goes first whatever its size),
+* advances the admitted lattices together through one ``Batch`` (two kernel
   launches per time step for the whole set, chunks replayed as CUDA graphs),
-  each lattice by exactly its own number of steps,
+  each lattice by exactly its own number of steps.  With ``fifo`` and
+  ``sjf`` every admitted lattice steps in every chunk, so they share the GPU
+  evenly.  With ``srpt`` (shortest remaining processing time) a chunk steps
+  only the lattices with the least work left (sites x remaining steps),
+  taken in that order until their sites reach ``fill_sites`` (enough to
+  fill the GPU), and pauses the others (``Batch.pause``): small requests
+  then finish at the speed they would have alone, instead of at the step
+  rate of the largest lattice beside them.  A lattice whose request has
+  waited longer than ``max_wait`` seconds comes first, so a large request
+  is not held back without end,
 * retires a lattice the moment its steps are done: reads its fields back to
   the host, frees its memory, and admits the next request in its place
   (continuous batching).
@@ -97,10 +106,11 @@ class Server:
     def __init__(self, lattice: str = "D3Q27", storage: str = "f16", inplace: bool = True, chunk: int = 16,
                  max_members: int = 64, hbm_budget: int | None = None, prep_threads: int = 4,
                  keep_fields: bool = False, stream=None, max_active_sites: int | None = None,
-                 policy: str = "fifo", max_wait: float = 5.0):
-        if policy not in ("fifo", "sjf"):
-            raise ValueError("policy is 'fifo' or 'sjf'")
+                 policy: str = "fifo", max_wait: float = 5.0, fill_sites: int = 1 << 21):
+        if policy not in ("fifo", "sjf", "srpt"):
+            raise ValueError("policy is 'fifo', 'sjf' or 'srpt'")
         self.policy, self.max_wait = policy, float(max_wait)
+        self.fill_sites = int(fill_sites)
         self.lattice, self.storage, self.inplace = lattice, storage, bool(inplace)
         self.chunk, self.max_members = int(chunk), int(max_members)
         self.max_active_sites = max_active_sites
@@ -131,6 +141,7 @@ class Server:
         stats = ServeStats()
         used = 0
         sites = 0
+        paused = {}                            # srpt: id(Lattice) -> paused now
         launches0 = self.batch.info()[1]
         with ThreadPoolExecutor(max_workers=self.prep_threads) as pool:
             t0 = clock()
@@ -140,7 +151,7 @@ class Server:
                     r = pend.popleft()
                     waiting.append((r, pool.submit(_prepare, r)))
                 # admission by free HBM and slots, in the policy's order
-                if self.policy == "sjf" and len(waiting) > 1:
+                if self.policy in ("sjf", "srpt") and len(waiting) > 1:
                     # requests waiting longer than max_wait first, in arrival
                     # order; then the least work (sites x steps) first
                     def key(rf, now=now):
@@ -180,6 +191,8 @@ class Server:
                     elif pend:
                         time.sleep(max(0.0, min(pend[0].arrival - (clock() - t0), 0.002)))
                     continue
+                if self.policy == "srpt":
+                    self._schedule(active, now, paused)
                 self.batch.step(self.chunk)
                 keep = []
                 for r, L, need, t_adm in active:
@@ -187,6 +200,7 @@ class Server:
                         out, failed = _read_result(L)
                         t_fin = clock() - t0
                         self.batch.remove(L)
+                        paused.pop(id(L), None)
                         L.close()
                         used -= need
                         sites -= L.N
@@ -199,6 +213,32 @@ class Server:
         stats.launches = self.batch.info()[1] - launches0
         stats.results.sort(key=lambda s: s.rid)
         return stats
+
+
+    def _schedule(self, active, now, paused):
+        """srpt: the lattices with the least work left step in the next chunk
+        (overdue requests first), until their sites reach fill_sites; the
+        others pause."""
+
+        def key(entry):
+            r, L = entry[0], entry[1]
+            if now - r.arrival > self.max_wait:
+                return (0, r.arrival)
+            return (1, L.N * self.batch.remaining(L))
+
+        run = set()
+        filled = 0
+        for entry in sorted(active, key=key):
+            if filled >= self.fill_sites:
+                break
+            run.add(id(entry[1]))
+            filled += entry[1].N
+        for entry in active:
+            L = entry[1]
+            want = id(L) not in run
+            if paused.get(id(L), False) != want:
+                self.batch.pause(L, want)
+                paused[id(L)] = want
 
 
 def _read_result(L: Lattice):

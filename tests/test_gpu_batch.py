@@ -199,3 +199,38 @@ def test_batch_autotune_keeps_results(lbm, storage):
             assert np.array_equal(x, y)
     for B, _ in (ref[0], tuned[0]):
         B.close()
+
+
+@pytest.mark.parametrize("storage", ["f64", "f16"])
+def test_paused_member_waits_and_resumes_bitwise(lbm, storage):
+    """lbm_batch_pause: a paused member takes no steps (its budget and state
+    stay) while the others advance; resumed, it ends bit for bit as it would
+    have without the pause, in FP64 also equal to the oracle.  Odd pause
+    lengths shift it against its batch-mates' in-place step parity."""
+    a, b = small_3d("D3Q27"), closed_box_3d("D3Q27")
+    B = lbm.Batch("D3Q27", storage)
+    A = make(lbm, a, storage, inplace=1)
+    O = make(lbm, b, storage)
+    B.add(A, 30)
+    B.add(O, 60)
+    B.step(7)
+    B.pause(A)
+    before = A.read_fields()
+    B.step(13)
+    assert B.remaining(A) == 23 and B.remaining(O) == 40
+    for x, y in zip(before, A.read_fields()):
+        assert np.array_equal(x, y)
+    B.pause(A, False)
+    assert B.step(100) == 2
+    R = make(lbm, a, storage, inplace=1)
+    B2 = lbm.Batch("D3Q27", storage)
+    B2.add(R, 30)
+    B2.step(30)
+    for x, y in zip(R.read_fields(), A.read_fields()):
+        assert np.array_equal(x, y)
+    if storage == "f64":
+        _, o = run_oracle(a, 30)
+        for x, y in zip(A.read_fields(), o):
+            assert np.array_equal(x, y)
+    with pytest.raises(lbm.LbmError):
+        B2.pause(O)                      # not a member of B2

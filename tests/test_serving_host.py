@@ -29,6 +29,7 @@ class FakeBatch:
 
     def __init__(self, lattice, storage):
         self.rem = {}
+        self.paused = set()
 
     def set_tuning(self, chunk=16, use_graph=True):
         pass
@@ -39,13 +40,20 @@ class FakeBatch:
 
     def remove(self, L):
         del self.rem[id(L)]
+        self.paused.discard(id(L))
+
+    def pause(self, L, paused=True):
+        assert id(L) in self.rem
+        (self.paused.add if paused else self.paused.discard)(id(L))
+        FakeBatch.log.append(("pause", int(paused)))
 
     def step(self, n):
-        for L, r in self.rem.values():
-            t = min(n, r)
-            L.steps_done += t
-        for v in self.rem.values():
-            v[1] -= min(n, v[1])
+        running = [v for k, v in self.rem.items() if k not in self.paused]
+        FakeBatch.log.append(("step", len(running)))
+        for v in running:
+            t = min(n, v[1])
+            v[0].steps_done += t
+            v[1] -= t
         return sum(1 for v in self.rem.values() if v[1] == 0)
 
     def remaining(self, L):
@@ -91,7 +99,7 @@ def test_admission_limits(fake):
     S = serving.Server("D3Q27", "f16", chunk=5, hbm_budget=1 << 40, max_active_sites=2 * 24 ** 3)
     st = S.run(reqs)
     assert len(st.results) == 20
-    assert max(n for _, n in FakeBatch.log) <= 8          # never more than the site cap allows of 16^3 lattices
+    assert max(n for e, n in FakeBatch.log if e == "add") <= 8   # never more than the site cap allows of 16^3 lattices
 
 
 def test_site_cap_still_admits_one_large_request(fake):
@@ -118,4 +126,34 @@ def test_sjf_admits_least_work_first(fake):
     S = serving.Server("D3Q27", "f16", chunk=4, hbm_budget=1 << 40, max_members=1, policy="sjf", max_wait=-1.0)
     st = S.run(reqs)
     order = [r.rid for r in sorted(st.results, key=lambda q: q.admitted)]
+    assert order == [r.rid for r in sorted(reqs, key=lambda q: q.arrival)]
+
+
+def _srpt_run(fake_batch_log, reqs, **kw):
+    ticks = iter(range(10 ** 9))
+    S = serving.Server("D3Q27", "f16", chunk=4, keep_fields=True, hbm_budget=1 << 40, policy="srpt", **kw)
+    return S.run(reqs, clock=lambda: next(ticks) * 1e-6)
+
+
+def test_srpt_order_and_pausing(fake):
+    """policy="srpt": every request admitted at t = 0, fill_sites below one
+    lattice, so one lattice steps per chunk: they finish in order of their
+    work (sites x steps), each with exactly its steps, while the others wait
+    paused.  A fill of all the sites steps everyone in every chunk; with
+    every request overdue (max_wait = -1) they run in arrival order."""
+    reqs = W.request_trace(n=9, rate=1e9, edges=(8, 12, 16), steps_range=(3, 30))
+    work = {r.rid: r.edge ** 3 * r.steps for r in reqs}
+    st = _srpt_run(FakeBatch.log, reqs, fill_sites=1, max_wait=1e9)
+    order = [r.rid for r in sorted(st.results, key=lambda q: q.finished)]
+    assert [work[i] for i in order] == sorted(work.values())
+    for r in st.results:
+        assert r.fields == (next(q.steps for q in reqs if q.rid == r.rid),)
+    assert {n for e, n in FakeBatch.log if e == "step"} == {1}
+    FakeBatch.log = []
+    st = _srpt_run(FakeBatch.log, reqs, fill_sites=1 << 40, max_wait=1e9)
+    assert not any(e == "pause" and n == 1 for e, n in FakeBatch.log)   # nobody waits
+    for r in st.results:
+        assert r.fields == (next(q.steps for q in reqs if q.rid == r.rid),)
+    st = _srpt_run(FakeBatch.log, reqs, fill_sites=1, max_wait=-1.0)
+    order = [r.rid for r in sorted(st.results, key=lambda q: q.finished)]
     assert order == [r.rid for r in sorted(reqs, key=lambda q: q.arrival)]
