@@ -94,6 +94,20 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def recorded_traffic(key: str, sites: int):
+    """DRAM bytes of one step of the workload `key` from the ncu record in
+    profiles/, scaled to `sites` by the sites of the capture; None unless the
+    record was taken on the kernel sources as they are now."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            ent = json.load(f).get(key, {})
+        if ent.get("source_hash") != kernel_source_hash():
+            return None
+        return int(round(ent["dram_bytes_per_site"] * sites))
+    except Exception:
+        return None
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -266,7 +280,9 @@ def storage_form(args, c, storage: str, f32_ms: float):
             "speedup_vs_f32": round(f32_ms / (ms / args.steps), 4),
             "dtype": f"{storage}-storage/f32", "form": form,
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "bytes_per_site": per_site, "peak_kind": peak_kind},
+                         "frac": round(achieved / peak, 4), "bytes_per_site": per_site, "peak_kind": peak_kind,
+                         "traffic": recorded_traffic(f"n{args.n}-{storage}-split", c.N)
+                         if form == "split form" and not args.inplace else None},
             "gpu_launches": (2 if form == "split form" else 1) * args.steps}
 
 
@@ -571,7 +587,9 @@ def run_bubble(args):
                        "parallelism": f"replicas x{world}",
                        "l2": f"inputs larger than L2 ({state_gb:.2f} GB state in the batch)"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+                         "frac": round(achieved / peak, 4),
+                         "traffic": recorded_traffic(f"{args.workload}-{args.storage}-batch", sites)
+                         if not args.inplace else None, "peak_kind": peak_kind,
                          "kernel": "batch_kernel<0> + batch_kernel<1> (split form over the batch)",
                          "store": "in-place AA" if args.inplace else "ping-pong", "bytes_per_site": per_site},
             "e2e": None, "gpu_launches": 2 * args.steps, "clocks": clk, "cpu_baseline": None,

@@ -236,9 +236,11 @@ int lbm_set_tuning(lbm_handle h, int variant, int zchunk);
 /* Shape of the cluster step (variant 5).  rows: CTAs per thread-block
  * cluster, one of 2, 4, 8, 16, or 0 for automatic (the largest the lattice
  * fits, 16 only where the device allows clusters of that non-portable
- * size).  staged: with FP32 arithmetic (FP32 or FP16 storage), 1 or -1
- * (default) stages the population rows each plane pulls in shared memory by
- * bulk asynchronous copies two planes ahead; 0 reads them from the store.
+ * size).  staged: with FP32 arithmetic (FP32 or FP16 storage), 1 stages
+ * the population rows each plane pulls in shared memory by bulk asynchronous
+ * copies two planes ahead; 0 or -1 (default) reads them from the store (on
+ * GB300 the staged form, one CTA per SM for its shared memory, was the
+ * slower one).
  * Neither changes results.  LBM_ERR_INVALID_ARG for other values,
  * LBM_ERR_UNSUPPORTED when the lattice does not meet the cluster step's
  * requirements with that many rows. */

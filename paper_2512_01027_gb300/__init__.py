@@ -370,7 +370,7 @@ class Lattice:
 
     def set_cluster(self, rows: int = 0, staged: int = -1):
         """Cluster step shape: CTAs (rows) per cluster (0 = auto) and whether the
-        pulled rows are staged by bulk copies (-1 = auto, 0 = no, 1 = yes)."""
+        pulled rows are staged by bulk copies (-1 = default, no; 0 = no; 1 = yes)."""
         _check(lib().lbm_set_cluster(self._h, int(rows), int(staged)), self._h)
 
     def debug_stall(self, plane: int):

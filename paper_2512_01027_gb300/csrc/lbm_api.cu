@@ -720,7 +720,7 @@ int lbm_set_cluster(lbm_handle h, int rows, int staged)
     if (rows != 0 && !h->ops->cluster_ok(h, rows))
         return fail(h, LBM_ERR_UNSUPPORTED, "the cluster step cannot use clusters of that many rows here");
     h->cluster_rows = rows;
-    h->cluster_stage = staged == 0 ? 0 : 1;
+    h->cluster_stage = staged == 1 ? 1 : 0;
     return LBM_OK;
 }
 

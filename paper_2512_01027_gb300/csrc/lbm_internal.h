@@ -85,7 +85,7 @@ struct lbm_ctx {
     int variant = 0;
     int cluster_rows = 0;          // CTAs (rows) per cluster of the cluster step (0: automatic)
     int cluster_zchunk = 0;        // planes per CTA of the cluster step (0: automatic)
-    int cluster_stage = 1;         // cluster step with FP32 arithmetic: rows staged by bulk copies (0: off)
+    int cluster_stage = 0;         // cluster step with FP32 arithmetic: rows staged by bulk copies (1: on)
     cudaStream_t stream = nullptr;
     int64_t steps = 0;
     std::string err;

@@ -502,17 +502,8 @@ __device__ __forceinline__ void moments_site(const SplitArgs<R, typename C::S> &
     }
 }
 
-// Load that bypasses L1 when CG: for data other blocks wrote earlier in the
-// same launch (the persistent step).
-template <bool CG, class T>
-__device__ __forceinline__ T ld_maybe_cg(const T *p)
-{
-    if constexpr (CG) return __ldcg(p);
-    else return *p;
-}
-
 // S0 + S2..S5 at site idx (0 <= idx < a.N).
-template <class L, class R, class C, bool HAS_MASK, int MODE, class IX, bool CG>
+template <class L, class R, class C, bool HAS_MASK, int MODE, class IX>
 __device__ __forceinline__ void collide_site_impl(const SplitArgs<R, typename C::S> &a, const int idx,
                                                   const uint32_t m)
 {
@@ -540,7 +531,7 @@ __device__ __forceinline__ void collide_site_impl(const SplitArgs<R, typename C:
         });
         static_for<0, NS>([&](auto J) {
             constexpr int j = decltype(J)::value;
-            pm[j] = ld_maybe_cg<CG>(a.PiG + eidx<IX>(j, N, idx));
+            pm[j] = a.PiG[eidx<IX>(j, N, idx)];
         });
     };
     if constexpr (kPacked<R>) {
@@ -548,11 +539,11 @@ __device__ __forceinline__ void collide_site_impl(const SplitArgs<R, typename C:
             load_h_pig();
             asm volatile("" ::: "memory");
         }
-        const float4 f0 = ld_maybe_cg<CG>(a.FB + idx);
+        const float4 f0 = a.FB[idx];
         u[0] = f0.x; u[1] = f0.y; u[2] = f0.z;
         phi = f0.w;
-        P = ld_maybe_cg<CG>(a.F_new + idx).w;
-        auto at = [&](auto I, int s) { return ld_maybe_cg<CG>(a.FB + nb.at<L, decltype(I)::value>(s)); };
+        P = a.F_new[idx].w;
+        auto at = [&](auto I, int s) { return a.FB[nb.at<L, decltype(I)::value>(s)]; };
         if (m == 0u) stencil_packed<L, false>(at, m, phi, gphi, lphi, gu);
         else stencil_packed<L, true>(at, m, phi, gphi, lphi, gu);
     } else {
@@ -616,7 +607,7 @@ __device__ __forceinline__ void collide_site_impl(const SplitArgs<R, typename C:
 // without bounce-back selections (the same arithmetic: with no mask bit set
 // both give the same bits).  Not in the even step of the in-place store:
 // there the two copies of the code need more registers than it has.
-template <class L, class R, class C, bool HAS_MASK, int MODE, class IX, bool CG = false>
+template <class L, class R, class C, bool HAS_MASK, int MODE, class IX>
 __device__ __forceinline__ void collide_site(const SplitArgs<R, typename C::S> &a, const int idx)
 {
     uint32_t m = 0;
@@ -624,12 +615,12 @@ __device__ __forceinline__ void collide_site(const SplitArgs<R, typename C::S> &
         m = a.mask[idx];
         if constexpr (kPacked<R> && MODE != kAAEven) {
             if (a.vote && !__any_sync(0xffffffffu, m != 0u)) {
-                collide_site_impl<L, R, C, false, MODE, IX, CG>(a, idx, 0u);
+                collide_site_impl<L, R, C, false, MODE, IX>(a, idx, 0u);
                 return;
             }
         }
     }
-    collide_site_impl<L, R, C, HAS_MASK, MODE, IX, CG>(a, idx, m);
+    collide_site_impl<L, R, C, HAS_MASK, MODE, IX>(a, idx, m);
 }
 
 // The u^{n+1} reading of the pressure formula's omega-term (coupling_unew):
