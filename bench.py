@@ -65,6 +65,10 @@ def parse():
     ap.add_argument("--serve-policy", default="srpt", choices=["fifo", "sjf", "srpt"],
                     help="batched server: admission in arrival order, or least work first; srpt also steps "
                          "only the lattices with the least work left in each chunk")
+    ap.add_argument("--serve-max-wait", type=float, default=5.0,
+                    help="sjf / srpt: seconds after which a waiting request goes first whatever its size")
+    ap.add_argument("--serve-solo", type=int, default=96 ** 3,
+                    help="srpt: requests of at least this many sites are stepped alone by the split kernels (0: none)")
     ap.add_argument("--serve-fill", type=int, default=1 << 21,
                     help="srpt: sites stepped per chunk (lattices with the least work left first)")
     ap.add_argument("--no-storage-forms", action="store_true",
@@ -204,7 +208,8 @@ def cpu_baseline(reps_target_s: float = 10.0):
             "sample": f"FP64 C oracle, D3Q27 droplet on film 64^3 (R = 8), {steps} steps, {dt:.1f} s"}
 
 
-def serving(n_requests: int, policy: str = "srpt", fill_sites: int = 1 << 21):
+def serving(n_requests: int, policy: str = "srpt", fill_sites: int = 1 << 21, max_wait: float = 5.0,
+            solo_sites: int = 96 ** 3):
     """Served solves/s and p50/p99 latency on the serving workload: the first
     n_requests of the seeded 2000-request trace (oscillating ellipsoidal
     droplets in periodic boxes of edge {32, 48, 64, 96, 128}, density ratio
@@ -216,12 +221,14 @@ def serving(n_requests: int, policy: str = "srpt", fill_sites: int = 1 << 21):
     policy: the batched server's order (sjf: admission by least work first,
     with a request waiting over 5 s going first; srpt: in addition, each
     chunk steps only the lattices with the least work left, up to fill_sites
-    sites, and pauses the others)."""
+    sites, and pauses the others; requests of at least solo_sites sites are
+    stepped alone by the split kernels in that same order)."""
     from paper_2512_01027_gb300.serving import Server, run_one_at_a_time
 
     full = 2000
     closed = W.request_trace(n=full, rate=1e9)[:n_requests]
-    srv = Server("D3Q27", "f16", inplace=True, chunk=16, policy=policy, fill_sites=fill_sites)
+    srv = Server("D3Q27", "f16", inplace=True, chunk=16, policy=policy, fill_sites=fill_sites, max_wait=max_wait,
+                 solo_sites=(solo_sites or None) if policy == "srpt" else None)
     cl = srv.run(closed).summary()
     cap = cl["solves_per_s"]
     rate = 0.8 * cap
@@ -234,6 +241,8 @@ def serving(n_requests: int, policy: str = "srpt", fill_sites: int = 1 << 21):
                         f"D3Q27 droplets, edges 32..128, 500..5000 steps, f16 storage, "
                         f"{work / 1e9:.0f} G site updates",
             "policy": policy, "fill_sites": fill_sites if policy == "srpt" else None,
+            "max_wait_s": max_wait if policy != "fifo" else None,
+            "solo_sites": solo_sites or None,
             "fraction_of_trace": n_requests / full,
             "closed_loop": cl, "open_loop": dict(op, arrival_rate_per_s=rate), "one_at_a_time_f32": seq}
 
@@ -451,7 +460,8 @@ def run_ours(args):
         L.close()
         del L
         torch.cuda.empty_cache()
-        serve = serving(args.serve_requests, args.serve_policy, args.serve_fill)
+        serve = serving(args.serve_requests, args.serve_policy, args.serve_fill, args.serve_max_wait,
+                        args.serve_solo)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

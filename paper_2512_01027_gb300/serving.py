@@ -25,7 +25,11 @@ surface tension, number of steps).  The server
   then finish at the speed they would have alone, instead of at the step
   rate of the largest lattice beside them.  A lattice whose request has
   waited longer than ``max_wait`` seconds comes first, so a large request
-  is not held back without end,
+  is not held back without end.  With ``solo_sites`` set, a request of at
+  least that many sites (one that fills the GPU by itself) is stepped by the
+  single-lattice split kernels instead of the batch kernel, in slices of
+  ``chunk`` steps taken in the same order; whether a request goes solo
+  depends on its size only, so its result still does not depend on the mix,
 * retires a lattice the moment its steps are done: reads its fields back to
   the host, frees its memory, and admits the next request in its place
   (continuous batching).
@@ -106,11 +110,15 @@ class Server:
     def __init__(self, lattice: str = "D3Q27", storage: str = "f16", inplace: bool = True, chunk: int = 16,
                  max_members: int = 64, hbm_budget: int | None = None, prep_threads: int = 4,
                  keep_fields: bool = False, stream=None, max_active_sites: int | None = None,
-                 policy: str = "fifo", max_wait: float = 5.0, fill_sites: int = 1 << 21):
+                 policy: str = "fifo", max_wait: float = 5.0, fill_sites: int = 1 << 21,
+                 solo_sites: int | None = None):
         if policy not in ("fifo", "sjf", "srpt"):
             raise ValueError("policy is 'fifo', 'sjf' or 'srpt'")
         self.policy, self.max_wait = policy, float(max_wait)
         self.fill_sites = int(fill_sites)
+        if solo_sites is not None and policy != "srpt":
+            raise ValueError("solo_sites needs policy 'srpt'")
+        self.solo_sites = solo_sites
         self.lattice, self.storage, self.inplace = lattice, storage, bool(inplace)
         self.chunk, self.max_members = int(chunk), int(max_members)
         self.max_active_sites = max_active_sites
@@ -142,6 +150,7 @@ class Server:
         used = 0
         sites = 0
         paused = {}                            # srpt: id(Lattice) -> paused now
+        solo = {}                              # srpt with solo_sites: id(Lattice) -> steps left
         launches0 = self.batch.info()[1]
         with ThreadPoolExecutor(max_workers=self.prep_threads) as pool:
             t0 = clock()
@@ -179,7 +188,10 @@ class Server:
                     L = Lattice(c.lattice, c.shape, periodic=c.periodic, solid=c.solid, storage=self.storage,
                                 g_ext=c.params.get("g_ext", (0, 0, 0)), inplace=int(self.inplace), **prm)
                     L.init_fields(c.phi0, c.P0, c.u0)
-                    self.batch.add(L, r.steps)
+                    if self.solo_sites is not None and n_sites >= self.solo_sites:
+                        solo[id(L)] = r.steps
+                    else:
+                        self.batch.add(L, r.steps)
                     used += need
                     sites += n_sites
                     active.append((r, L, need, clock() - t0))
@@ -191,15 +203,37 @@ class Server:
                     elif pend:
                         time.sleep(max(0.0, min(pend[0].arrival - (clock() - t0), 0.002)))
                     continue
-                if self.policy == "srpt":
-                    self._schedule(active, now, paused)
-                self.batch.step(self.chunk)
+                lone = self._schedule(active, now, paused, solo) if self.policy == "srpt" else None
+                diverged = set()
+                if lone is not None:
+                    k = min(self.chunk, solo[id(lone)])
+                    lone.step(k)
+                    solo[id(lone)] -= k
+                    try:
+                        lone.check()                   # waits for the slice
+                    except LbmError as e:
+                        if e.code != LBM_ERR_NONFINITE:
+                            raise
+                        diverged.add(id(lone))
+                        solo[id(lone)] = 0
+                else:
+                    self.batch.step(self.chunk)
                 keep = []
                 for r, L, need, t_adm in active:
-                    if self.batch.remaining(L) == 0:
-                        out, failed = _read_result(L)
+                    if id(L) in solo:
+                        done = solo[id(L)] == 0
+                    else:
+                        done = self.batch.remaining(L) == 0
+                    if done:
+                        if id(L) in diverged:
+                            out, failed = None, True
+                        else:
+                            out, failed = _read_result(L)
                         t_fin = clock() - t0
-                        self.batch.remove(L)
+                        if id(L) in solo:
+                            del solo[id(L)]
+                        else:
+                            self.batch.remove(L)
                         paused.pop(id(L), None)
                         L.close()
                         used -= need
@@ -215,30 +249,42 @@ class Server:
         return stats
 
 
-    def _schedule(self, active, now, paused):
+    def _schedule(self, active, now, paused, solo):
         """srpt: the lattices with the least work left step in the next chunk
         (overdue requests first), until their sites reach fill_sites; the
-        others pause."""
+        others pause.  Returns the solo lattice to step instead of the batch
+        when one comes first in that order, else None."""
+
+        def left(L):
+            return solo[id(L)] if id(L) in solo else self.batch.remaining(L)
 
         def key(entry):
             r, L = entry[0], entry[1]
             if now - r.arrival > self.max_wait:
                 return (0, r.arrival)
-            return (1, L.N * self.batch.remaining(L))
+            return (1, L.N * left(L))
 
+        order = sorted(active, key=key)
+        if order and id(order[0][1]) in solo:
+            return order[0][1]
         run = set()
         filled = 0
-        for entry in sorted(active, key=key):
+        for entry in order:
             if filled >= self.fill_sites:
                 break
+            if id(entry[1]) in solo:
+                continue
             run.add(id(entry[1]))
             filled += entry[1].N
         for entry in active:
             L = entry[1]
+            if id(L) in solo:
+                continue
             want = id(L) not in run
             if paused.get(id(L), False) != want:
                 self.batch.pause(L, want)
                 paused[id(L)] = want
+        return None
 
 
 def _read_result(L: Lattice):

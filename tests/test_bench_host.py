@@ -21,3 +21,29 @@ def test_algorithmic_bytes_per_site(Q, D, store, field, expected):
 def test_replica_throughput_counts_every_rank():
     # 2 replicas of 1e6 sites, 100 steps in 50 ms on the slowest rank
     assert bench.replica_mlups(10 ** 6, 100, 50.0, 2) == pytest.approx(4000.0)
+
+
+def test_recorded_traffic_follows_the_source_hash(tmp_path, monkeypatch):
+    """The DRAM traffic of a workload is reported only while the kernel
+    sources hash to the value recorded with it, scaled by sites; otherwise
+    (or with no record) it is None."""
+    import json
+
+    rec = tmp_path / "traffic.json"
+    rec.write_text(json.dumps({"w": {"source_hash": "abc", "dram_bytes_per_site": 629.2}}))
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(rec))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "abc")
+    assert bench.recorded_traffic("w", 1000) == 629200
+    assert bench.recorded_traffic("other", 1000) is None
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "changed")
+    assert bench.recorded_traffic("w", 1000) is None
+
+
+def test_committed_traffic_record_matches_the_sources():
+    """profiles/step_kernel_traffic.json was captured on the kernel sources as
+    they are: the bench's traffic fields are live, not stale."""
+    import json
+
+    rec = json.load(open(bench.TRAFFIC_FILE))
+    for key in ("n256-f32-split", "n256-f16-split", "bubble1-f32-batch"):
+        assert rec[key]["source_hash"] == bench.kernel_source_hash(), key

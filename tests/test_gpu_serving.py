@@ -71,3 +71,26 @@ def test_one_at_a_time_baseline_runs(lbm):
     st = run_one_at_a_time(reqs)
     assert len(st.results) == 3
     assert st.summary()["solves_per_s"] > 0
+
+
+def test_srpt_with_solo_requests_alone_equals_mixed(lbm):
+    """policy="srpt" with solo_sites: requests of 24^3 sites and more are
+    stepped alone by the split kernels, the others in the batch with
+    pausing; each result equals, bit for bit, the same request served by
+    itself with the same settings (the path depends on its size only)."""
+    from paper_2512_01027_gb300.serving import Server
+
+    reqs = small_trace(n=7, rate=1e6)
+    kw = dict(chunk=8, keep_fields=True, hbm_budget=2 << 30, policy="srpt", fill_sites=20 ** 3,
+              solo_sites=24 ** 3)
+    S = Server("D3Q27", "f16", **kw)
+    mixed = S.run(reqs)
+    S.close()
+    assert len(mixed.results) == len(reqs)
+    assert any(r.edge ** 3 >= 24 ** 3 for r in reqs) and any(r.edge ** 3 < 24 ** 3 for r in reqs)
+    for r, got in zip(sorted(reqs, key=lambda q: q.rid), mixed.results):
+        A = Server("D3Q27", "f16", **kw)
+        alone = A.run([W.Request(r.rid, 0.0, r.edge, r.R, r.ratio, r.sigma, r.steps)]).results[0]
+        A.close()
+        for x, y in zip(alone.fields, got.fields):
+            assert np.array_equal(x, y)

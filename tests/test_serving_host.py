@@ -20,6 +20,13 @@ class FakeLattice:
     def read_fields(self):
         return (self.steps_done,)
 
+    def step(self, n):                 # stepped alone (srpt with solo_sites)
+        self.steps_done += n
+        FakeBatch.log.append(("solo", self.N))
+
+    def check(self):
+        pass
+
     def close(self):
         self.closed = True
 
@@ -37,6 +44,7 @@ class FakeBatch:
     def add(self, L, steps):
         self.rem[id(L)] = [L, steps]
         FakeBatch.log.append(("add", len(self.rem)))
+        FakeBatch.log.append(("add_sites", L.N))
 
     def remove(self, L):
         del self.rem[id(L)]
@@ -157,3 +165,20 @@ def test_srpt_order_and_pausing(fake):
     st = _srpt_run(FakeBatch.log, reqs, fill_sites=1, max_wait=-1.0)
     order = [r.rid for r in sorted(st.results, key=lambda q: q.finished)]
     assert order == [r.rid for r in sorted(reqs, key=lambda q: q.arrival)]
+
+
+def test_srpt_steps_large_requests_alone(fake):
+    """solo_sites: a request of at least that many sites never joins the
+    batch; it is stepped alone in chunk-sized slices in the same
+    least-work-left order, and still gets exactly its steps."""
+    reqs = W.request_trace(n=9, rate=1e9, edges=(8, 12, 16), steps_range=(3, 30))
+    work = {r.rid: r.edge ** 3 * r.steps for r in reqs}
+    st = _srpt_run(FakeBatch.log, reqs, fill_sites=1, max_wait=1e9, solo_sites=16 ** 3)
+    for r in st.results:
+        assert r.fields == (next(q.steps for q in reqs if q.rid == r.rid),)
+    assert all(n < 16 ** 3 for e, n in FakeBatch.log if e == "add_sites")
+    assert any(e == "solo" and n == 16 ** 3 for e, n in FakeBatch.log)
+    order = [r.rid for r in sorted(st.results, key=lambda q: q.finished)]
+    assert [work[i] for i in order] == sorted(work.values())
+    with pytest.raises(ValueError):
+        serving.Server("D3Q27", "f16", hbm_budget=1 << 40, policy="sjf", solo_sites=1)
