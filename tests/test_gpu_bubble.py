@@ -101,3 +101,39 @@ def test_bubble_f32_phase_mass(lbm, case):
     L.step(20000)
     L.check()
     assert abs(L.reduce()["mass"] / m0 - 1) <= 1e-4
+
+
+@pytest.mark.parametrize("case", [1, 2])
+def test_bubble_batch_as_benchmarked(lbm, case):
+    """The launch configuration bench.py --workload bubble1/2 times: 32
+    lattices of the case in one FP32 batch at the shape lbm_batch_autotune
+    picks.  Every member ends bit for bit like every other, and against the
+    FP64 oracle after 50 steps phi is within 1e-5 (measured 3.7e-6), P within
+    1e-4 of max|P| (measured 1.7e-5) and u within 2e-4 of max|u| (measured
+    7e-5; u is still 1e-6, near the FP32 floor of the populations that carry
+    it, see test_bubble_f32_tracks_f64)."""
+    c = W.rising_bubble_2d(case)
+    prm = {k: v for k, v in c.params.items() if k != "g_ext"}
+    steps = 50
+    B = lbm.Batch("D2Q9", "f32")
+    lats = []
+    for _ in range(32):
+        L = lbm.Lattice(c.lattice, c.shape, periodic=c.periodic, solid=c.solid, storage="f32",
+                        g_ext=c.params["g_ext"], **prm)
+        L.init_fields(c.phi0, c.P0, c.u0)
+        B.add(L, steps + 1000)
+        lats.append(L)
+    B.autotune(32)                               # restores every member's state and budget
+    B.step(steps)
+    _, (fo, Po, uo) = run_oracle(c, steps)
+    first = lats[0].read_fields()
+    for L in lats[1:]:
+        for x, y in zip(first, L.read_fields()):
+            assert np.array_equal(x, y)
+    f, P, u = first
+    assert np.abs(f - fo).max() <= 1e-5
+    assert np.abs(P - Po).max() <= 1e-4 * np.abs(Po).max()
+    assert np.abs(u - uo).max() <= 2e-4 * np.abs(uo).max()
+    B.close()
+    for L in lats:
+        L.close()
