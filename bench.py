@@ -69,6 +69,9 @@ def parse():
                     help="sjf / srpt: seconds after which a waiting request goes first whatever its size")
     ap.add_argument("--serve-solo", type=int, default=96 ** 3,
                     help="srpt: requests of at least this many sites are stepped alone by the split kernels (0: none)")
+    ap.add_argument("--serve-solo-preempt", action="store_true",
+                    help="srpt: a solo request may be preempted by one with less work left (default: once "
+                         "started, it runs to its end)")
     ap.add_argument("--serve-fill", type=int, default=1 << 21,
                     help="srpt: sites stepped per chunk (lattices with the least work left first)")
     ap.add_argument("--no-storage-forms", action="store_true",
@@ -209,7 +212,7 @@ def cpu_baseline(reps_target_s: float = 10.0):
 
 
 def serving(n_requests: int, policy: str = "srpt", fill_sites: int = 1 << 21, max_wait: float = 5.0,
-            solo_sites: int = 96 ** 3):
+            solo_sites: int = 96 ** 3, solo_to_end: bool = True):
     """Served solves/s and p50/p99 latency on the serving workload: the first
     n_requests of the seeded 2000-request trace (oscillating ellipsoidal
     droplets in periodic boxes of edge {32, 48, 64, 96, 128}, density ratio
@@ -222,13 +225,14 @@ def serving(n_requests: int, policy: str = "srpt", fill_sites: int = 1 << 21, ma
     with a request waiting over 5 s going first; srpt: in addition, each
     chunk steps only the lattices with the least work left, up to fill_sites
     sites, and pauses the others; requests of at least solo_sites sites are
-    stepped alone by the split kernels in that same order)."""
+    stepped alone by the split kernels in that same order and, with
+    solo_to_end, run to their end once started)."""
     from paper_2512_01027_gb300.serving import Server, run_one_at_a_time
 
     full = 2000
     closed = W.request_trace(n=full, rate=1e9)[:n_requests]
     srv = Server("D3Q27", "f16", inplace=True, chunk=16, policy=policy, fill_sites=fill_sites, max_wait=max_wait,
-                 solo_sites=(solo_sites or None) if policy == "srpt" else None)
+                 solo_sites=(solo_sites or None) if policy == "srpt" else None, solo_to_end=solo_to_end)
     cl = srv.run(closed).summary()
     cap = cl["solves_per_s"]
     rate = 0.8 * cap
@@ -242,7 +246,7 @@ def serving(n_requests: int, policy: str = "srpt", fill_sites: int = 1 << 21, ma
                         f"{work / 1e9:.0f} G site updates",
             "policy": policy, "fill_sites": fill_sites if policy == "srpt" else None,
             "max_wait_s": max_wait if policy != "fifo" else None,
-            "solo_sites": solo_sites or None,
+            "solo_sites": solo_sites or None, "solo_to_end": solo_to_end,
             "fraction_of_trace": n_requests / full,
             "closed_loop": cl, "open_loop": dict(op, arrival_rate_per_s=rate), "one_at_a_time_f32": seq}
 
@@ -466,7 +470,7 @@ def run_ours(args):
         del L
         torch.cuda.empty_cache()
         serve = serving(args.serve_requests, args.serve_policy, args.serve_fill, args.serve_max_wait,
-                        args.serve_solo)
+                        args.serve_solo, not args.serve_solo_preempt)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -28,8 +28,10 @@ surface tension, number of steps).  The server
   is not held back without end.  With ``solo_sites`` set, a request of at
   least that many sites (one that fills the GPU by itself) is stepped by the
   single-lattice split kernels instead of the batch kernel, in slices of
-  ``chunk`` steps taken in the same order; whether a request goes solo
-  depends on its size only, so its result still does not depend on the mix,
+  ``chunk`` steps taken in the same order (with ``solo_to_end``, once its
+  first slice is taken it runs to its end, so smaller arrivals no longer
+  stretch the largest requests); whether a request goes solo depends on its
+  size only, so its result still does not depend on the mix,
 * retires a lattice the moment its steps are done: reads its fields back to
   the host, frees its memory, and admits the next request in its place
   (continuous batching).
@@ -111,7 +113,7 @@ class Server:
                  max_members: int = 64, hbm_budget: int | None = None, prep_threads: int = 4,
                  keep_fields: bool = False, stream=None, max_active_sites: int | None = None,
                  policy: str = "fifo", max_wait: float = 5.0, fill_sites: int = 1 << 21,
-                 solo_sites: int | None = None):
+                 solo_sites: int | None = None, solo_to_end: bool = False):
         if policy not in ("fifo", "sjf", "srpt"):
             raise ValueError("policy is 'fifo', 'sjf' or 'srpt'")
         self.policy, self.max_wait = policy, float(max_wait)
@@ -119,6 +121,8 @@ class Server:
         if solo_sites is not None and policy != "srpt":
             raise ValueError("solo_sites needs policy 'srpt'")
         self.solo_sites = solo_sites
+        self.solo_to_end = bool(solo_to_end)   # a solo request, once started, runs to its end
+        self._solo_running = None
         self.lattice, self.storage, self.inplace = lattice, storage, bool(inplace)
         self.chunk, self.max_members = int(chunk), int(max_members)
         self.max_active_sites = max_active_sites
@@ -150,6 +154,7 @@ class Server:
         used = 0
         sites = 0
         paused = {}                            # srpt: id(Lattice) -> paused now
+        self._solo_running = None
         solo = {}                              # srpt with solo_sites: id(Lattice) -> steps left
         launches0 = self.batch.info()[1]
         with ThreadPoolExecutor(max_workers=self.prep_threads) as pool:
@@ -264,8 +269,14 @@ class Server:
                 return (0, r.arrival)
             return (1, L.N * left(L))
 
+        if self.solo_to_end and self._solo_running is not None:
+            for entry in active:
+                if entry[1] is self._solo_running and solo.get(id(entry[1]), 0) > 0:
+                    return entry[1]
+            self._solo_running = None
         order = sorted(active, key=key)
         if order and id(order[0][1]) in solo:
+            self._solo_running = order[0][1]
             return order[0][1]
         run = set()
         filled = 0

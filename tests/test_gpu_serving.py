@@ -73,7 +73,8 @@ def test_one_at_a_time_baseline_runs(lbm):
     assert st.summary()["solves_per_s"] > 0
 
 
-def test_srpt_with_solo_requests_alone_equals_mixed(lbm):
+@pytest.mark.parametrize("to_end", [False, True])
+def test_srpt_with_solo_requests_alone_equals_mixed(lbm, to_end):
     """policy="srpt" with solo_sites: requests of 24^3 sites and more are
     stepped alone by the split kernels, the others in the batch with
     pausing; each result equals, bit for bit, the same request served by
@@ -82,7 +83,7 @@ def test_srpt_with_solo_requests_alone_equals_mixed(lbm):
 
     reqs = small_trace(n=7, rate=1e6)
     kw = dict(chunk=8, keep_fields=True, hbm_budget=2 << 30, policy="srpt", fill_sites=20 ** 3,
-              solo_sites=24 ** 3)
+              solo_sites=24 ** 3, solo_to_end=to_end)
     S = Server("D3Q27", "f16", **kw)
     mixed = S.run(reqs)
     S.close()

@@ -23,6 +23,7 @@ class FakeLattice:
     def step(self, n):                 # stepped alone (srpt with solo_sites)
         self.steps_done += n
         FakeBatch.log.append(("solo", self.N))
+        FakeBatch.events.append(id(self))
 
     def check(self):
         pass
@@ -33,6 +34,7 @@ class FakeLattice:
 
 class FakeBatch:
     log = []
+    events = []                        # what each chunk stepped: a solo lattice's id, or "batch"
 
     def __init__(self, lattice, storage):
         self.rem = {}
@@ -58,6 +60,7 @@ class FakeBatch:
     def step(self, n):
         running = [v for k, v in self.rem.items() if k not in self.paused]
         FakeBatch.log.append(("step", len(running)))
+        FakeBatch.events.append("batch")
         for v in running:
             t = min(n, v[1])
             v[0].steps_done += t
@@ -81,6 +84,7 @@ def fake(monkeypatch):
     monkeypatch.setattr(serving, "_prepare", lambda r: W.Case("c", "D3Q27", (r.edge,) * 3, W.base_params(), 0, 0, 0,
                                                              (1, 1, 1), None, r.steps))
     FakeBatch.log = []
+    FakeBatch.events = []
 
 
 def trace(n=12):
@@ -182,3 +186,19 @@ def test_srpt_steps_large_requests_alone(fake):
     assert [work[i] for i in order] == sorted(work.values())
     with pytest.raises(ValueError):
         serving.Server("D3Q27", "f16", hbm_budget=1 << 40, policy="sjf", solo_sites=1)
+
+
+def test_srpt_solo_to_end_runs_a_started_solo_request_through(fake):
+    """solo_to_end: once a solo request has taken its first slice, nothing
+    else steps until its last one; every request still gets exactly its
+    steps."""
+    reqs = W.request_trace(n=9, rate=1e9, edges=(8, 12, 16), steps_range=(3, 30))
+    st = _srpt_run(FakeBatch.log, reqs, fill_sites=1, max_wait=1e9, solo_sites=16 ** 3, solo_to_end=True)
+    for r in st.results:
+        assert r.fields == (next(q.steps for q in reqs if q.rid == r.rid),)
+    ev = FakeBatch.events
+    solos = {e for e in ev if e != "batch"}
+    assert solos
+    for s in solos:
+        idx = [i for i, e in enumerate(ev) if e == s]
+        assert idx == list(range(idx[0], idx[-1] + 1)), "a solo request was interrupted"
