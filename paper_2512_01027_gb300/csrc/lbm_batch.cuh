@@ -73,7 +73,9 @@ constexpr int batch_min_blocks()
 }
 
 // The item t of member j (base: its first site for this thread) in PHASE.
-template <class L, class R, class C, int PHASE>
+// PP: every member of the chunk uses the ping-pong store, so only that
+// stream mode's code is compiled in.
+template <class L, class R, class C, int PHASE, bool PP>
 __device__ __forceinline__ void batch_item(const SplitArgs<R, typename C::S> &a, int mode, bool masked,
                                            long long base, int span)
 {
@@ -90,7 +92,10 @@ __device__ __forceinline__ void batch_item(const SplitArgs<R, typename C::S> &a,
             const long long lidx = base + (long long)s * kSplitThreads;
             if (lidx >= a.N) break;   // past the member's last site (so are the item's later blocks)
             const int idx = (int)lidx;
-            if (masked) {
+            if constexpr (PP) {
+                if (masked) batch_site<L, R, C, PHASE, true, kPingPong>(a, idx);
+                else batch_site<L, R, C, PHASE, false, kPingPong>(a, idx);
+            } else if (masked) {
                 if (mode == kPingPong) batch_site<L, R, C, PHASE, true, kPingPong>(a, idx);
                 else if (mode == kAAOdd) batch_site<L, R, C, PHASE, true, kAAOdd>(a, idx);
                 else batch_site<L, R, C, PHASE, true, kAAEven>(a, idx);
@@ -106,7 +111,7 @@ __device__ __forceinline__ void batch_item(const SplitArgs<R, typename C::S> &a,
 // PHASE 0: S0 + S1 of every member; PHASE 1: S0 + S2..S5; PHASE 2 (between
 // the two, when some member takes it): the u^{n+1} coupling's omega-term of
 // P^{n+1} for those members.
-template <class L, class R, class C, int PHASE>
+template <class L, class R, class C, int PHASE, bool PP = false>
 __global__ void __launch_bounds__(kSplitThreads, batch_min_blocks<L, R, C, PHASE>())
     batch_kernel(const BatchHeader *__restrict__ hdr, const BatchMember<R, typename C::S> *__restrict__ mem, int k)
 {
@@ -121,11 +126,11 @@ __global__ void __launch_bounds__(kSplitThreads, batch_min_blocks<L, R, C, PHASE
         const bool masked = mem[j].has_mask != 0;
         const long long base = (t - mem[j].first_item) * span * kSplitThreads + threadIdx.x;
         if constexpr (kBatchArgsByRef<L, R, C>) {
-            batch_item<L, R, C, PHASE>(mem[j].a[q], mode, masked, base, span);
+            batch_item<L, R, C, PHASE, PP>(mem[j].a[q], mode, masked, base, span);
         } else {
             SplitArgs<R, S> a = mem[j].a[q];
             a.seed += (unsigned)(k - q);   // a[q] holds the chunk's first steps; step k of the chunk
-            batch_item<L, R, C, PHASE>(a, mode, masked, base, span);
+            batch_item<L, R, C, PHASE, PP>(a, mode, masked, base, span);
         }
     }
 }

@@ -56,10 +56,11 @@ int ensure_table(lbm_batch_ctx *b, size_t members)
 }
 
 // Executable graph of one chunk of K steps: table upload + 2K launches (3K
-// with a coupled member).
+// with a coupled member), with the ping-pong-only kernels when every member
+// uses that store.
 int graph_for(lbm_batch_ctx *b, int K, cudaGraphExec_t *out)
 {
-    const int key = 2 * K + (b->coupled ? 1 : 0);
+    const int key = 4 * K + (b->pp ? 2 : 0) + (b->coupled ? 1 : 0);
     for (auto &g : b->graphs)
         if (g.first == key) {
             *out = g.second;
@@ -69,7 +70,7 @@ int graph_for(lbm_batch_ctx *b, int K, cudaGraphExec_t *out)
     int rc = bcuda(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
     if (rc != LBM_OK) return rc;
     cudaError_t e1 = cudaMemcpyAsync(b->d_table, b->h_table, b->table_bytes, cudaMemcpyHostToDevice, b->stream);
-    cudaError_t e2 = b->ops->batch_launch(b->stream, b->d_table, K, b->grid[0], b->grid[1], b->coupled);
+    cudaError_t e2 = b->ops->batch_launch(b->stream, b->d_table, K, b->grid[0], b->grid[1], b->coupled, b->pp);
     cudaError_t e3 = cudaStreamEndCapture(b->stream, &graph);
     rc = bcuda(b, e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3), "graph capture");
     if (rc != LBM_OK) {
@@ -253,9 +254,11 @@ int lbm_batch_step(lbm_batch b, int64_t n, int *finished)
         char *mem = static_cast<char *>(b->h_table) + batch_header_bytes();
         long long first = 0;
         b->coupled = false;
+        b->pp = true;
         for (size_t r = 0; r < order.size(); ++r) {
             const lbm_ctx *h = b->members[order[r]];
             if (h->consts.coupling) b->coupled = true;
+            if (h->inplace) b->pp = false;
             b->ops->batch_fill(h, take[order[r]], first, mem + r * mbytes);
             const long long items = b->ops->batch_items(h, b->span);
             for (int k = 0; k < take[order[r]]; ++k) hdr.active[k] += items;
@@ -272,7 +275,8 @@ int lbm_batch_step(lbm_batch b, int64_t n, int *finished)
             rc = bcuda(b, cudaMemcpyAsync(b->d_table, b->h_table, b->table_bytes, cudaMemcpyHostToDevice, b->stream),
                        "H2D batch table");
             if (rc == LBM_OK)
-                rc = bcuda(b, b->ops->batch_launch(b->stream, b->d_table, K, b->grid[0], b->grid[1], b->coupled),
+                rc = bcuda(b, b->ops->batch_launch(b->stream, b->d_table, K, b->grid[0], b->grid[1], b->coupled,
+                                                   b->pp),
                            "batch launch");
         }
         // the pinned table is rewritten for the next chunk: wait for this one

@@ -276,15 +276,20 @@ struct Impl {
         return per_sm * (sms > 0 ? sms : 1);
     }
 
-    static cudaError_t batch_launch(cudaStream_t s, const void *d_table, int K, int grid0, int grid1, bool coupled)
+    static cudaError_t batch_launch(cudaStream_t s, const void *d_table, int K, int grid0, int grid1, bool coupled,
+                                    bool pp)
     {
         const BatchHeader *hdr = static_cast<const BatchHeader *>(d_table);
         const BatchMember<R, S> *mem = reinterpret_cast<const BatchMember<R, S> *>(
             static_cast<const char *>(d_table) + batch_header_bytes());
+        // pp: every member uses the ping-pong store (kernels with that mode only);
+        // the grids sized for the general kernels fit these as well
         for (int k = 0; k < K; ++k) {
-            batch_kernel<L, R, C, 0><<<grid0, kSplitThreads, 0, s>>>(hdr, mem, k);
+            if (pp) batch_kernel<L, R, C, 0, true><<<grid0, kSplitThreads, 0, s>>>(hdr, mem, k);
+            else batch_kernel<L, R, C, 0><<<grid0, kSplitThreads, 0, s>>>(hdr, mem, k);
             if (coupled) batch_kernel<L, R, C, 2><<<grid1, kSplitThreads, 0, s>>>(hdr, mem, k);
-            batch_kernel<L, R, C, 1><<<grid1, kSplitThreads, 0, s>>>(hdr, mem, k);
+            if (pp) batch_kernel<L, R, C, 1, true><<<grid1, kSplitThreads, 0, s>>>(hdr, mem, k);
+            else batch_kernel<L, R, C, 1><<<grid1, kSplitThreads, 0, s>>>(hdr, mem, k);
         }
         return cudaGetLastError();
     }

@@ -110,8 +110,9 @@ struct lbm_batch_ctx {
     size_t cap_members = 0;
     void *d_table = nullptr;
     void *h_table = nullptr;          // pinned staging copy
-    std::vector<std::pair<int, cudaGraphExec_t>> graphs;   // per (chunk length, coupled): key 2 K + coupled
+    std::vector<std::pair<int, cudaGraphExec_t>> graphs;   // per (chunk length, coupled, pp): key 4 K + 2 pp + coupled
     bool coupled = false;             // the current table has a member with the u^{n+1} coupling
+    bool pp = false;                  // every member of the current table uses the ping-pong store
     int grid[2] = {0, 0};
     int span = 1;                     // 128-site blocks per work item
     int blocks_per_sm = 0;            // persistent blocks per SM (0: the kernels' occupancy)
@@ -142,7 +143,9 @@ struct Ops {
     void (*batch_fill)(const lbm_ctx *c, int take, long long first_item, void *dst);
     int (*batch_grid)(int phase, int blocks_per_sm);
     // coupled: some member takes the u^{n+1} coupling (a third launch per step)
-    cudaError_t (*batch_launch)(cudaStream_t s, const void *d_table, int K, int grid0, int grid1, bool coupled);
+    // pp: every member uses the ping-pong store
+    cudaError_t (*batch_launch)(cudaStream_t s, const void *d_table, int K, int grid0, int grid1, bool coupled,
+                                bool pp);
     // cluster step (variant 5) with `rows` CTAs per cluster
     bool (*cluster_ok)(const lbm_ctx *c, int rows);
 };
