@@ -156,6 +156,7 @@ class Server:
         paused = {}                            # srpt: id(Lattice) -> paused now
         self._solo_running = None
         solo = {}                              # srpt with solo_sites: id(Lattice) -> steps left
+        solo_launches = 0                      # the split form's two launches per solo step
         launches0 = self.batch.info()[1]
         with ThreadPoolExecutor(max_workers=self.prep_threads) as pool:
             t0 = clock()
@@ -214,6 +215,7 @@ class Server:
                     k = min(self.chunk, solo[id(lone)])
                     lone.step(k)
                     solo[id(lone)] -= k
+                    solo_launches += 2 * k
                     try:
                         lone.check()                   # waits for the slice
                     except LbmError as e:
@@ -249,7 +251,7 @@ class Server:
                         keep.append((r, L, need, t_adm))
                 active = keep
             stats.makespan = clock() - t0
-        stats.launches = self.batch.info()[1] - launches0
+        stats.launches = self.batch.info()[1] - launches0 + solo_launches
         stats.results.sort(key=lambda s: s.rid)
         return stats
 
